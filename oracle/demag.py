@@ -1,0 +1,144 @@
+"""Demag field as a discrete convolution (Sec. 4.4).  TEST INFRASTRUCTURE ONLY.
+
+Sec. 4.4 discretises the demag field as h_i = sum_j N_{i-j} M_j with
+M = Ms m.  With the positive-trace tensor of ``oracle.newell`` this reads
+
+    h_i = - sum_j N(i - j) (Ms_j m_j).
+
+Two independent routes are provided:
+
+* ``demag_direct`` / ``demag_direct_c``: the definition, summed term by term
+  (NumPy per target cell, or plain C with one OpenMP thread per target cell);
+* ``demag_fft``: the zero-padded FFT convolution Sec. 4.4 describes ("zero
+  padding of the magnetization ... point-wise multiplication in Fourier
+  space"), with numpy.fft over a padding P_a = 2 n_a (P_a = 1 where n_a = 1).
+
+Padding reading: a linear convolution of length n needs P >= 2n - 1.  With
+P = 2n the wrapped offset index n is never used by a valid output; it is set
+to 0 (keeps the tensor's parity symmetry exact).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from .newell import COMPS
+
+
+def _full(Nt):
+    """(6, ...) component array -> (3, 3, ...) symmetric view."""
+    T = np.empty((3, 3) + Nt.shape[1:])
+    for c, (a, b) in enumerate(COMPS):
+        T[a, b] = Nt[c]
+        T[b, a] = Nt[c]
+    return T
+
+
+def magnetization(m, Ms):
+    """M = Ms m, with Ms a scalar or an (nx, ny, nz) array."""
+    Ms = np.broadcast_to(np.asarray(Ms, dtype=np.float64), m.shape[:3])
+    return m * Ms[..., None]
+
+
+def demag_direct(Nt, M):
+    """h_i = -sum_j N(i-j) M_j, summed target by target (small grids)."""
+    nx, ny, nz = M.shape[:3]
+    T = _full(Nt)
+    h = np.zeros_like(M)
+    si, sj, sk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                oi = i - si + nx - 1
+                oj = j - sj + ny - 1
+                ok = k - sk + nz - 1
+                Nij = T[:, :, oi, oj, ok]  # (3, 3, nx, ny, nz)
+                h[i, j, k] = -np.einsum("abxyz,xyzb->a", Nij, M)
+    return h
+
+
+_CLIB = None
+
+
+def _clib():
+    """Load (building if needed) the plain-C brute-force sum in direct_demag.c."""
+    global _CLIB
+    if _CLIB is None:
+        here = os.path.dirname(os.path.abspath(__file__))
+        so = os.path.join(here, "_direct_demag.so")
+        src = os.path.join(here, "direct_demag.c")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            build_c()
+        lib = ctypes.CDLL(so)
+        lib.direct_demag.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 3
+        lib.direct_demag.restype = None
+        _CLIB = lib
+    return _CLIB
+
+
+def build_c():
+    """Compile oracle/direct_demag.c into oracle/_direct_demag.so with gcc."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    so = os.path.join(here, "_direct_demag.so")
+    src = os.path.join(here, "direct_demag.c")
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", so, src])
+    return so
+
+
+def demag_direct_c(Nt, M):
+    """Same definition as demag_direct, summed in plain C (OpenMP over targets)."""
+    nx, ny, nz = M.shape[:3]
+    Nt = np.ascontiguousarray(Nt, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    assert Nt.shape == (6, 2 * nx - 1, 2 * ny - 1, 2 * nz - 1)
+    h = np.zeros_like(M)
+    _clib().direct_demag(nx, ny, nz, Nt.ctypes.data, M.ctypes.data, h.ctypes.data)
+    return h
+
+
+def padded_shape(n):
+    return tuple(1 if v == 1 else 2 * v for v in n)
+
+
+def periodic_kernel(Nt, n):
+    """Embed the offset tensor into the periodic P-grid: entry a holds N(a)
+    for 0 <= a <= n-1, N(a - P) for P-n+1 <= a <= P-1, and 0 otherwise."""
+    P = padded_shape(n)
+    out = np.zeros((6,) + P)
+    idx = []
+    for v, p in zip(n, P):
+        src = np.array([a if a <= v - 1 else a - p for a in range(p)])
+        valid = np.array([(a <= v - 1) or (a >= p - v + 1) for a in range(p)])
+        idx.append((src + v - 1, valid))
+    (ix, vx), (iy, vy), (iz, vz) = idx
+    sub = Nt[:, ix][:, :, iy][:, :, :, iz]
+    mask = vx[:, None, None] & vy[None, :, None] & vz[None, None, :]
+    out[:] = np.where(mask[None], sub, 0.0)
+    return out
+
+
+def tensor_spectrum(Nt, n):
+    """rfftn of the six periodic tensor components over the padded grid."""
+    P = padded_shape(n)
+    K = periodic_kernel(Nt, n)
+    return np.stack([np.fft.rfftn(K[c], s=P, axes=(0, 1, 2)) for c in range(6)])
+
+
+def demag_fft(Nt, M, Nhat=None):
+    """h = -N * M by zero-padded FFT convolution over P = 2n (Sec. 4.4)."""
+    n = M.shape[:3]
+    P = padded_shape(n)
+    if Nhat is None:
+        Nhat = tensor_spectrum(Nt, n)
+    Mhat = [np.fft.rfftn(M[..., b], s=P, axes=(0, 1, 2)) for b in range(3)]
+    h = np.empty_like(M)
+    for a in range(3):
+        acc = np.zeros_like(Mhat[0])
+        for c, (p, q) in enumerate(COMPS):
+            if p == a:
+                acc = acc + Nhat[c] * Mhat[q]
+            elif q == a:
+                acc = acc + Nhat[c] * Mhat[p]
+        h[..., a] = -np.fft.irfftn(acc, s=P, axes=(0, 1, 2))[: n[0], : n[1], : n[2]]
+    return h

@@ -1,0 +1,126 @@
+"""Pins for the oracle's exchange (Sec. 4.2), anisotropy (Sec. 4.1), Zeeman
+and energies (Eq. linear_energy_discrete)."""
+import numpy as np
+import pytest
+
+from oracle.constants import MU0
+from oracle.fields import (anisotropy_field, exchange_field, linear_energy,
+                           zeeman_energy, zeeman_field)
+
+
+def test_uniform_magnetisation_has_no_exchange_field():
+    n = (7, 4, 3)
+    rng = np.random.default_rng(0)
+    A = rng.uniform(0.5e-11, 2e-11, size=n)
+    Ms = rng.uniform(5e5, 1e6, size=n)
+    m = np.broadcast_to(np.array([0.6, 0.0, 0.8]), n + (3,)).copy()
+    h = exchange_field(m, Ms, A, (2e-9, 3e-9, 1e-9))
+    assert np.all(h == 0.0)
+
+
+def test_spin_spiral_closed_form():
+    """m = (cos kx, sin kx, 0): every interior cell has
+    h = 2A/(mu0 Ms) * 2 (cos k dx - 1)/dx^2 * m."""
+    nx, dx, k = 40, 2e-9, 0.31 / 2e-9
+    n = (nx, 3, 2)
+    x = (np.arange(nx) * dx)[:, None, None] * np.ones(n)
+    m = np.stack([np.cos(k * x), np.sin(k * x), np.zeros(n)], axis=-1)
+    A, Ms = 1.3e-11, 8e5
+    h = exchange_field(m, Ms, A, (dx, 1e-9, 1e-9))
+    expect = (2 * A / (MU0 * Ms)) * 2 * (np.cos(k * dx) - 1) / dx ** 2 * m
+    inner = slice(1, nx - 1)
+    scale = np.max(np.abs(expect))
+    assert np.max(np.abs(h[inner] - expect[inner])) < 1e-12 * scale
+    # Neumann boundary: the first cell only sees its +x neighbour
+    h0 = (2 * A / (MU0 * Ms)) * (m[1] - m[0]) / dx ** 2
+    assert np.max(np.abs(h[0] - h0)) < 1e-12 * scale
+
+
+def test_homogeneous_A_reduces_to_laplacian():
+    """With constant A the harmonic-mean form equals the paper's simplified
+    second-difference form (Sec. 4.2), with the missing neighbour of a
+    boundary cell replaced by the cell itself (zero normal derivative)."""
+    n = (6, 5, 4)
+    d = (1e-9, 2e-9, 1.5e-9)
+    rng = np.random.default_rng(1)
+    m = rng.normal(size=n + (3,))
+    A, Ms = 1.5e-11, 1e6
+    h = exchange_field(m, Ms, A, d)
+    pad = np.pad(m, ((1, 1), (1, 1), (1, 1), (0, 0)), mode="edge")
+    lap = np.zeros_like(m)
+    c = (slice(1, -1),) * 3
+    for ax in range(3):
+        up = list(c)
+        dn = list(c)
+        up[ax] = slice(2, None)
+        dn[ax] = slice(0, -2)
+        lap += (pad[tuple(up)] - 2 * m + pad[tuple(dn)]) / d[ax] ** 2
+    ref = 2 * A / (MU0 * Ms) * lap
+    assert np.max(np.abs(h - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_exchange_energy_is_sum_over_links():
+    """E = -1/2 mu0 V sum Ms m.h_ex equals V sum_links c_ij |m_i - m_j|^2 with
+    c_ij = (2/d^2) A_i A_j / (A_i + A_j), for any m and any A."""
+    n = (5, 4, 3)
+    d = (1e-9, 2e-9, 3e-9)
+    V = d[0] * d[1] * d[2]
+    rng = np.random.default_rng(2)
+    m = rng.normal(size=n + (3,))
+    A = rng.uniform(0.5e-11, 2e-11, size=n)
+    Ms = rng.uniform(5e5, 1e6, size=n)
+    E = linear_energy(m, exchange_field(m, Ms, A, d), Ms, V)
+    ref = 0.0
+    for idx in np.ndindex(*n):
+        for ax in range(3):
+            j = list(idx)
+            j[ax] += 1
+            if j[ax] >= n[ax]:
+                continue
+            j = tuple(j)
+            c = (2 / d[ax] ** 2) * A[idx] * A[j] / (A[idx] + A[j])
+            ref += V * c * np.sum((m[idx] - m[j]) ** 2)
+    assert abs(E - ref) < 1e-12 * abs(ref)
+
+
+def test_zero_Ms_cells_carry_no_local_field():
+    n = (4, 3, 2)
+    m = np.random.default_rng(3).normal(size=n + (3,))
+    Ms = np.full(n, 8e5)
+    Ms[1, 1, 0] = 0.0
+    h = exchange_field(m, Ms, 1e-11, (1e-9,) * 3)
+    ha = anisotropy_field(m, Ms, 5e3, (0.0, 0.0, 1.0))
+    assert np.all(h[1, 1, 0] == 0) and np.all(ha[1, 1, 0] == 0)
+    assert np.all(np.isfinite(h)) and np.all(np.isfinite(ha))
+
+
+def test_anisotropy_closed_forms():
+    n = (3, 2, 2)
+    e = np.array([1.0, 2.0, 2.0]) / 3.0
+    Ku, Ms, V = 4e5, 1e6, 8e-27
+    m_par = np.broadcast_to(e, n + (3,)).copy()
+    h = anisotropy_field(m_par, Ms, Ku, e)
+    assert np.allclose(h, 2 * Ku / (MU0 * Ms) * m_par, rtol=1e-14, atol=0)
+    perp = np.array([2.0, -1.0, 0.0]) / np.sqrt(5.0)
+    m_perp = np.broadcast_to(perp, n + (3,)).copy()
+    assert np.max(np.abs(anisotropy_field(m_perp, Ms, Ku, e))) < 1e-20 * Ku / (MU0 * Ms) + 1e-9
+    # E_u = -Ku V sum (e.m)^2
+    rng = np.random.default_rng(4)
+    m = rng.normal(size=n + (3,))
+    m /= np.linalg.norm(m, axis=-1, keepdims=True)
+    E = linear_energy(m, anisotropy_field(m, Ms, Ku, e), Ms, V)
+    assert abs(E + Ku * V * np.sum((m @ e) ** 2)) < 1e-12 * Ku * V * m[..., 0].size
+
+
+def test_zeeman_field_and_energy():
+    n = (2, 2, 1)
+    B = 0.010                       # 10 mT
+    h = zeeman_field((B / MU0, 0.0, 0.0), n)
+    assert abs(h[0, 0, 0, 0] - 7957.747154594767) < 1e-9
+    m = np.zeros(n + (3,))
+    m[..., 0] = 1.0
+    Ms, V = 8e5, 1e-27
+    assert abs(zeeman_energy(m, h, Ms, V) + 4 * Ms * V * B) < 1e-12 * 4 * Ms * V * B
+    w = np.array([[[1.0], [0.0]], [[0.5], [2.0]]])
+    hw = zeeman_field((1.0, 2.0, 3.0), n, w)
+    assert np.allclose(hw[1, 0, 0], [0.5, 1.0, 1.5]) and np.all(hw[0, 1, 0] == 0)
