@@ -1,0 +1,197 @@
+/*
+ * mm.h -- C ABI of libmm.so, a GB300 (sm_103a) implementation of the hot path
+ * of the finite-difference micromagnetic method of arXiv 2302.08843
+ * (magnum.np): one effective-field evaluation (demag, exchange, uniaxial
+ * anisotropy, Zeeman), the LLG right-hand side and the Runge-Kutta stage
+ * update on a regular cell grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid (Sec. 2): nx x ny x nz cells of size dx x dy x dz metres, cell centre
+ *   (i dx, j dy, k dz).  Cell index c = i + nx * (j + ny * k) (x fastest).
+ * Vector fields (m, h): structure of arrays, three planes of nx*ny*nz values,
+ *   [3][nz][ny][nx].  Their element type is the state's "real": double for
+ *   MM_FP64, float for MM_FP32_FIELDS.  Fields are in A/m, m is unit length.
+ * Scalar material maps: nx*ny*nz doubles in the same cell order.
+ * Pointers: caller memory is borrowed for the duration of the call only; a
+ *   flag says whether it is host or device memory (device memory must be on the
+ *   state's device).  The state owns all of its device buffers.
+ * Streams: all GPU work of a state is enqueued on the CUDA stream given at
+ *   creation (NULL = the legacy default stream).  Functions return after
+ *   enqueueing, except those that return host scalars (E_out, DP45 step
+ *   acceptance, mm_relax, mm_get_m to host), which synchronise that stream.
+ * Errors: every function returns an mm_status; mm_last_error() gives a
+ *   thread-local message for the last failure.  Nothing aborts or throws.
+ * Cells with Ms = 0 carry no effective field (the nan_to_num of the
+ *   anisotropy listing in Sec. 4.1, applied to every term).
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_state mm_state;   /* opaque, library-owned */
+
+typedef enum {
+    MM_OK = 0,
+    MM_EINVAL = 1,          /* bad argument (null pointer, size, enum)          */
+    MM_ENOMEM = 2,          /* device or host allocation failed                 */
+    MM_ECUDA = 3,           /* a CUDA call failed (message says which)           */
+    MM_ENONFINITE = 4,      /* a NaN or Inf appeared in m or in a reduction      */
+    MM_ESTEP = 5,           /* DP45 step size underflow (dt < 1e-22 s)           */
+    MM_ENOTCONVERGED = 6,   /* mm_relax reached max_steps                        */
+    MM_ETIMEOUT = 7,        /* reserved: a bounded device-side wait gave up      */
+    MM_ENOTSETUP = 8        /* mm_demag_setup / mm_set_m / mm_set_material missing */
+} mm_status;
+
+typedef enum {
+    MM_FP64 = 0,            /* every array and all arithmetic in double          */
+    MM_FP32_FIELDS = 1      /* m, fields, FFT and stencil in float; the Newell
+                               tensor is built in double, reductions, the DP45
+                               error norm and time are accumulated in double     */
+} mm_precision;
+
+typedef enum { MM_RK4 = 0, MM_DP45 = 1 } mm_method;
+
+typedef struct {
+    int nx, ny, nz;          /* cells per axis, each >= 1, nx*ny*nz < 2^31       */
+    double dx, dy, dz;       /* cell size in metres, > 0                         */
+} mm_grid;
+
+/* Material (Sec. 2 material dict; Sec. 4.1, 4.2, Eq. llg).  Each scalar is
+ * used for every cell unless the matching per-cell pointer is non-NULL.
+ * Easy axis: ku_axis for every cell, or, if grain_id is non-NULL, row
+ * grain_id[c] of ku_axis_table (ngrains x 3 doubles, unit vectors).
+ * All pointers are host or device memory according to the flag passed to
+ * mm_set_material; the data is copied into the state. */
+typedef struct {
+    double Ms;               /* saturation magnetisation, A/m                    */
+    double A;                /* exchange constant, J/m                            */
+    double Ku1;              /* first-order uniaxial anisotropy constant, J/m^3  */
+    double alpha;            /* Gilbert damping                                  */
+    double ku_axis[3];       /* unit easy axis                                   */
+    const double* Ms_cell;   /* nx*ny*nz or NULL                                 */
+    const double* A_cell;
+    const double* Ku1_cell;
+    const double* alpha_cell;
+    const double* ku_axis_table;  /* ngrains x 3 or NULL                         */
+    const uint8_t* grain_id;      /* nx*ny*nz or NULL                            */
+    int ngrains;                  /* 1..256 when grain_id is given               */
+} mm_material;
+
+/* Uniform time-dependent external field h(t) in A/m, evaluated on the host at
+ * every stage time t (seconds). */
+typedef void (*mm_field_fn)(double t, double h_out[3], void* user);
+
+/* Create a state for one grid.  cuda_stream is a cudaStream_t (NULL allowed).
+ * Allocates the state's device buffers on the current device.  Padded FFT
+ * extents are the next power of two >= 2 n per axis (1 for an axis with one
+ * cell); each padded extent must be <= 4096.  Fails with MM_EINVAL for bad
+ * sizes, MM_ENOMEM if the buffers do not fit. */
+mm_status mm_state_create(const mm_grid* grid, mm_precision precision, void* cuda_stream,
+                          mm_state** out);
+
+/* Release every buffer of the state (NULL is a no-op).  Synchronises its stream. */
+void mm_state_destroy(mm_state* s);
+
+/* Copy the material into the state (Sec. 2 material dict; Sec. 4.1, 4.2).
+ * ptrs_on_device: 0 = host pointers, 1 = device pointers.  Checks Ms >= 0,
+ * A >= 0, alpha >= 0 for the scalar values and ngrains in 1..256. */
+mm_status mm_set_material(mm_state* s, const mm_material* mat, int ptrs_on_device);
+
+/* Copy m (SoA [3][nz][ny][nx], the state's real type) into the state.  The
+ * values are taken as given (no normalisation).  Resets the DP45 first stage. */
+mm_status mm_set_m(mm_state* s, const void* m, int on_device);
+
+/* Copy the state's m out (same layout and type).  A host copy synchronises. */
+mm_status mm_get_m(const mm_state* s, void* m_out, int on_device);
+
+/* External field (Zeeman): h_i(t) = w_i * h(t), with h(t) = fn(t) if fn is
+ * non-NULL, else h_const (A/m).  weight: nx*ny*nz doubles or NULL (w = 1),
+ * host or device according to on_device. */
+mm_status mm_set_zeeman(mm_state* s, const double h_const[3], mm_field_fn fn, void* user,
+                        const double* weight, int on_device);
+
+/* Build the demag tensor (Sec. 4.4): Newell's cell-averaged tensor where the
+ * Chebyshev cell distance is <= p_newell, the point dipole of Eq. dipole
+ * beyond (p_newell < 0: Newell everywhere), in double precision on the host,
+ * then its real, six-component Fourier spectrum over the padded grid, scaled
+ * by -1/(Px Py Pz) and stored on the device in the state's real type.
+ * A state without this call has no demag term (MM_ENOTSETUP from mm_heff and
+ * the integrators unless mm_demag_disable was called). */
+mm_status mm_demag_setup(mm_state* s, int p_newell);
+
+/* Run without a demag term (tests and macrospin problems). */
+mm_status mm_demag_disable(mm_state* s);
+
+/* One effective-field evaluation (Sec. 4) at time t on m (device pointer in
+ * the state's layout and type, or NULL for the state's m).  h_out: device
+ * buffer for the total field or NULL.  E_out: host array of 4 doubles or NULL,
+ * receives (E_demag, E_exchange, E_anisotropy, E_zeeman) in joules
+ * (Eq. linear_energy_discrete for the first three, -mu0 V sum Ms m.h for
+ * Zeeman); asking for E_out synchronises the stream.  torque_out: host double
+ * or NULL, receives max over cells of |m x h| / Ms (synchronises). */
+mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], double t,
+                  double* torque_out);
+
+/* Advance the state by one step of the LLG equation (Eq. llg).
+ * MM_RK4: one classic RK4 step of size *dt_inout from *t_inout (four field
+ *   evaluations; enqueue only, no synchronisation).
+ * MM_DP45: Dormand-Prince 5(4) with first-same-as-last; tries *dt_inout,
+ *   shrinks it until the error norm max |y5 - y4| / (rtol + rtol max(|y_n|,|y5|))
+ *   is <= 1, returns with the step accepted, *dt_inout set to the proposed next
+ *   step (dt * min(5, max(0.2, 0.9 err^-1/5))).  Synchronises once per attempt
+ *   to read the error norm.  MM_ESTEP if dt falls below 1e-22 s.
+ * On return *t_inout is advanced by the step taken.  m is renormalised to
+ * unit length after each step.  MM_ENONFINITE if the step produced NaN/Inf
+ * (DP45 only; RK4 checks nothing to stay asynchronous). */
+mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rtol,
+                      double* t_inout);
+
+/* Relax (Sec. 3): DP45 steps with the material's damping until
+ * max_i |m_i x h_i| / Ms_i < tol (the field of the last stage of the accepted
+ * step), or max_steps accepted steps (then MM_ENOTCONVERGED).  Starts from
+ * dt = *dt_inout (1e-13 s if *dt_inout <= 0) and time *t_inout; both are
+ * updated.  steps_out, torque_out: host outputs or NULL. */
+mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* dt_inout,
+                   double* t_inout, int* steps_out, double* torque_out);
+
+/* Host-only helper (no GPU): the real-space demag tensor this library builds
+ * (Sec. 4.4, same rule as mm_demag_setup) for every cell offset, as
+ * 6 x (2nx-1) x (2ny-1) x (2nz-1) doubles, components (xx, xy, xz, yy, yz, zz),
+ * offset (i, j, k) at [c][i+nx-1][j+ny-1][k+nz-1].  out must hold that many. */
+mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out);
+
+/* Host-only helper (no GPU): the real Fourier spectrum mm_demag_setup builds,
+ * over the padded grid Px x Py x Pz of mm_state_create, for the octant
+ * kz <= Pz/2, ky <= Py/2, kx <= Px/2, as 6 x (Pz/2+1) x (Py/2+1) x (Px/2+1)
+ * doubles (kx fastest), already multiplied by -1/(Px Py Pz). */
+mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out);
+
+/* Padded FFT extents and the row stride of the x-spectrum of a state
+ * (out: Px, Py, Pz, Kx = Px/2+1, Kx_stride). */
+mm_status mm_state_info(const mm_state* s, int out[5]);
+
+/* Per-kernel timing with CUDA events recorded on the state's stream.
+ * mm_profile_enable(s, 1) starts recording (clears totals); 0 stops.
+ * mm_profile_read synchronises and returns, for up to max kernels, the name,
+ * the launch count and the summed device time in milliseconds. */
+mm_status mm_profile_enable(mm_state* s, int on);
+int       mm_profile_read(mm_state* s, const char** names, int* counts, double* ms, int max);
+
+/* Thread-local description of the last error (never NULL). */
+const char* mm_last_error(void);
+
+/* Library version string. */
+const char* mm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

@@ -142,3 +142,21 @@ def demag_fft(Nt, M, Nhat=None):
                 acc = acc + Nhat[c] * Mhat[p]
         h[..., a] = -np.fft.irfftn(acc, s=P, axes=(0, 1, 2))[: n[0], : n[1], : n[2]]
     return h
+
+
+def rounding_sensitivity(n, dx, p, M, scales=(1e9, 3.7e8)):
+    """The oracle's own floating-point sensitivity of h = -N * M to the
+    rounding of Newell's formula: the tensor is dimensionless, so evaluating
+    it with the cell sizes expressed in other units (dx * s) must give the same
+    tensor; the largest relative max-norm change of h over the scales is the
+    noise floor of a double-precision evaluation (the 27-term sum of Sec. 4.4
+    cancels about (r/dx)^6 at offset r).  Used to state the FP64 parity bound
+    as max(1e-10, 2 x this)."""
+    from .newell import demag_tensor
+    h = demag_fft(demag_tensor(n, dx, p), M)
+    sc = np.max(np.abs(h))
+    worst = 0.0
+    for s in scales:
+        hs = demag_fft(demag_tensor(n, tuple(v * s for v in dx), p), M)
+        worst = max(worst, float(np.max(np.abs(hs - h)) / sc))
+    return worst

@@ -1,0 +1,89 @@
+// Internal interfaces between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mm {
+
+struct DemagDims {
+    int nx, ny, nz;      // cells
+    int LX, LY, LZ;      // padded FFT extents
+    int KX;              // LX/2 + 1 spectrum columns
+    int KXS;             // row stride of S1/S2 and of the tensor spectrum (elements)
+};
+
+// CUDA-event timing of kernel launches on a stream (inactive unless enabled).
+struct KernelTimer {
+    bool on = false;
+    struct Rec { int name; cudaEvent_t a, b; };
+    std::vector<std::string> names;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    int cur = -1;
+    cudaEvent_t cur_a = nullptr;
+    void begin(cudaStream_t st, const char* name);
+    void end(cudaStream_t st);
+    void reset();
+    void destroy();
+};
+
+template <typename T>
+void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typename Cplx<T>::type* S1,
+                 typename Cplx<T>::type* S2, const T* tens, T* h, cudaStream_t st, KernelTimer* tm);
+
+// number of doubles per block in the reduction partials
+constexpr int kNPart = 8;
+// partial / scalar slots
+enum { R_TORQUE = 0, R_EDEM = 1, R_EEX = 2, R_EANI = 3, R_EZEE = 4, R_ERR = 5, R_NONFINITE = 6 };
+
+template <typename T>
+struct StageParams {
+    int nx, ny, nz;
+    long N;
+    double V;                    // cell volume
+    T idx2, idy2, idz2;          // 1 / d^2 per axis
+    const T* m;                  // stage input (SoA)
+    const T* hd;                 // demag field (SoA) or null
+    const T* Ms_cell; T Ms;
+    const T* A_cell; T A;
+    const T* Ku_cell; T Ku;
+    const T* alpha_cell; T alpha;
+    const uint8_t* grain; const T* axis_tab; T ex, ey, ez;
+    const T* zw; T hx0, hy0, hz0;
+    T* h_out;                    // total effective field or null
+    T* k_out;                    // stage derivative or null
+    const T* mn;                 // m at the start of the step
+    T* next;                     // mn + dt (sum_j kc_j kin_j + ck k), or null
+    const T* kin[7];
+    double kc[7];
+    int nk;
+    double ck;
+    double dt;
+    int renorm;
+    const T* acc_in;             // acc_out = acc_in + acc_b k (acc_in may be null)
+    T* acc_out;
+    double acc_b;
+    double eb[7];                // error e = dt (sum_j eb_j kin_j + eb_k k)
+    double eb_k;
+    double rtol, atol;
+    int want_err, want_energy, want_torque;
+    double* partials;            // [gridDim.x][kNPart]
+};
+
+template <typename T> void launch_stage(const StageParams<T>& p, cudaStream_t st, int* nblocks);
+void launch_finalize(const double* partials, int nblocks, double* scalars, cudaStream_t st);
+template <typename T> void launch_convert(const double* src, T* dst, long n, cudaStream_t st);
+template <typename T> void launch_renorm_copy(const T* src, T* dst, long N, cudaStream_t st);
+template <typename T> void launch_combine(const T* mn, const T* const* kin, const double* kc, int nk, double dt,
+                                          T* out, long N, cudaStream_t st);
+// copy the host-built twiddle table into the FFT kernels' device table (current device)
+cudaError_t upload_twiddles(const double2* w64, const float2* w32);
+
+}  // namespace mm

@@ -1,0 +1,742 @@
+// C ABI of libmm.so (declarations and contracts in include/mm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "demag.h"
+#include "mm.h"
+#include "tensor_host.h"
+
+using namespace mm;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+mm_status fail(mm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define MM_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);               \
+    } while (0)
+
+#define MM_LAUNCHED()                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(MM_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define MM_TRY(expr)                     \
+    do {                                 \
+        mm_status s_ = (expr);           \
+        if (s_ != MM_OK) return s_;      \
+    } while (0)
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+std::mutex g_tw_mu;
+bool g_tw_done[128] = {false};
+
+mm_status ensure_twiddles(int dev) {
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    if (dev < 0 || dev >= 128) return fail(MM_EINVAL, "device ordinal %d out of range", dev);
+    if (g_tw_done[dev]) return MM_OK;
+    std::vector<double> re, im;
+    twiddle_table(kMaxFft, re, im);
+    std::vector<double2> w64(kMaxFft);
+    std::vector<float2> w32(kMaxFft);
+    for (int i = 0; i < kMaxFft; ++i) {
+        w64[i] = make_double2(re[i], im[i]);
+        w32[i] = make_float2((float)re[i], (float)im[i]);
+    }
+    MM_CUDA(upload_twiddles(w64.data(), w32.data()));
+    g_tw_done[dev] = true;
+    return MM_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- timer ----
+namespace mm {
+void KernelTimer::begin(cudaStream_t st, const char* name) {
+    if (!on) return;
+    int id = -1;
+    for (size_t i = 0; i < names.size(); ++i)
+        if (names[i] == name) { id = (int)i; break; }
+    if (id < 0) { names.emplace_back(name); id = (int)names.size() - 1; }
+    while (pool.size() < used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        pool.push_back(e);
+    }
+    cur = id;
+    cur_a = pool[used++];
+    cudaEventRecord(cur_a, st);
+}
+void KernelTimer::end(cudaStream_t st) {
+    if (!on || cur < 0) return;
+    cudaEvent_t b = pool[used++];
+    cudaEventRecord(b, st);
+    recs.push_back({cur, cur_a, b});
+    cur = -1;
+}
+void KernelTimer::reset() {
+    recs.clear();
+    used = 0;
+    cur = -1;
+}
+void KernelTimer::destroy() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    recs.clear();
+    used = 0;
+}
+}  // namespace mm
+
+// --------------------------------------------------------------- state ----
+struct mm_state {
+    mm_grid g{};
+    mm_precision prec = MM_FP64;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    DemagDims d{};
+    long N = 0;
+    size_t rsz = 8;          // sizeof(real)
+    size_t csz = 16;         // sizeof(complex)
+    // device buffers
+    void* m = nullptr;       // 3N, the state's magnetisation
+    void* mA = nullptr;      // 3N stage inputs (ping)
+    void* mB = nullptr;      // 3N stage inputs (pong)
+    void* acc = nullptr;     // 3N RK4 weighted sum
+    void* hd = nullptr;      // 3N demag field
+    void* S1 = nullptr;      // 3 ny nz KXS complex
+    void* S2 = nullptr;      // 3 nz Py KXS complex (Py > 1)
+    void* tens = nullptr;    // 6 KZ2 KY2 KXS real
+    void* K[7] = {nullptr};  // DP45 stage derivatives
+    void* Ms_cell = nullptr;
+    void* A_cell = nullptr;
+    void* Ku_cell = nullptr;
+    void* alpha_cell = nullptr;
+    void* axis_tab = nullptr;
+    uint8_t* grain = nullptr;
+    void* zw = nullptr;
+    double* partials = nullptr;
+    int part_cap = 0;
+    double* scalars = nullptr;     // device kNPart
+    double* h_scalars = nullptr;   // pinned host kNPart
+    // material and field
+    double Ms = 0, A = 0, Ku = 0, alpha = 0, axis[3] = {1, 0, 0};
+    double h0[3] = {0, 0, 0};
+    mm_field_fn fn = nullptr;
+    void* user = nullptr;
+    bool have_m = false, have_mat = false, demag_ready = false, demag_off = false;
+    bool fsal = false;
+    KernelTimer timer;
+};
+
+namespace {
+
+mm_status dev_alloc(void** p, size_t bytes) {
+    if (bytes == 0) { *p = nullptr; return MM_OK; }
+    MM_CUDA(cudaMalloc(p, bytes));
+    return MM_OK;
+}
+
+void dev_free(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+mm_status check_state(const mm_state* s) {
+    if (!s) return fail(MM_EINVAL, "null state");
+    return MM_OK;
+}
+
+mm_status set_device(const mm_state* s) {
+    MM_CUDA(cudaSetDevice(s->device));
+    return MM_OK;
+}
+
+mm_status ensure_partials(mm_state* s, int nblocks) {
+    if (nblocks <= s->part_cap) return MM_OK;
+    dev_free(reinterpret_cast<void*&>(s->partials));
+    MM_TRY(dev_alloc(reinterpret_cast<void**>(&s->partials), sizeof(double) * kNPart * (size_t)nblocks));
+    s->part_cap = nblocks;
+    return MM_OK;
+}
+
+// upload a per-cell (or small) double array into a device buffer of the state's real type
+mm_status upload_real(mm_state* s, const double* src, long n, int on_device, void** dst) {
+    dev_free(*dst);
+    if (!src) return MM_OK;
+    MM_TRY(dev_alloc(dst, s->rsz * (size_t)n));
+    if (on_device) {
+        if (s->prec == MM_FP64) {
+            MM_CUDA(cudaMemcpyAsync(*dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
+        } else {
+            launch_convert<float>(src, (float*)*dst, n, s->st);
+            MM_LAUNCHED();
+        }
+    } else {
+        if (s->prec == MM_FP64) {
+            MM_CUDA(cudaMemcpyAsync(*dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
+            MM_CUDA(cudaStreamSynchronize(s->st));
+        } else {
+            std::vector<float> tmp(n);
+            for (long i = 0; i < n; ++i) tmp[i] = (float)src[i];
+            MM_CUDA(cudaMemcpyAsync(*dst, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s->st));
+            MM_CUDA(cudaStreamSynchronize(s->st));
+        }
+    }
+    return MM_OK;
+}
+
+mm_status ready_for_fields(const mm_state* s) {
+    if (!s->have_mat) return fail(MM_ENOTSETUP, "mm_set_material has not been called");
+    if (!s->demag_ready && !s->demag_off) return fail(MM_ENOTSETUP, "mm_demag_setup has not been called");
+    return MM_OK;
+}
+
+void zeeman_at(const mm_state* s, double t, double h[3]) {
+    if (s->fn) {
+        s->fn(t, h, s->user);
+    } else {
+        h[0] = s->h0[0]; h[1] = s->h0[1]; h[2] = s->h0[2];
+    }
+}
+
+template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, const void* m, double t) {
+    std::memset(&p, 0, sizeof(p));
+    p.nx = s->g.nx; p.ny = s->g.ny; p.nz = s->g.nz;
+    p.N = s->N;
+    p.V = s->g.dx * s->g.dy * s->g.dz;
+    p.idx2 = (T)(1.0 / (s->g.dx * s->g.dx));
+    p.idy2 = (T)(1.0 / (s->g.dy * s->g.dy));
+    p.idz2 = (T)(1.0 / (s->g.dz * s->g.dz));
+    p.m = (const T*)m;
+    p.hd = s->demag_off ? nullptr : (const T*)s->hd;
+    p.Ms_cell = (const T*)s->Ms_cell; p.Ms = (T)s->Ms;
+    p.A_cell = (const T*)s->A_cell; p.A = (T)s->A;
+    p.Ku_cell = (const T*)s->Ku_cell; p.Ku = (T)s->Ku;
+    p.alpha_cell = (const T*)s->alpha_cell; p.alpha = (T)s->alpha;
+    p.grain = s->grain; p.axis_tab = (const T*)s->axis_tab;
+    p.ex = (T)s->axis[0]; p.ey = (T)s->axis[1]; p.ez = (T)s->axis[2];
+    p.zw = (const T*)s->zw;
+    double h[3];
+    zeeman_at(s, t, h);
+    p.hx0 = (T)h[0]; p.hy0 = (T)h[1]; p.hz0 = (T)h[2];
+    p.mn = (const T*)s->m;
+}
+
+// demag field of m into s->hd
+template <typename T> mm_status run_demag(mm_state* s, const void* m) {
+    if (s->demag_off) return MM_OK;
+    using C = typename Cplx<T>::type;
+    demag_apply<T>(s->d, (const T*)m, (const T*)s->Ms_cell, (T)s->Ms, (C*)s->S1, (C*)s->S2, (const T*)s->tens,
+                   (T*)s->hd, s->st, &s->timer);
+    MM_LAUNCHED();
+    return MM_OK;
+}
+
+template <typename T> mm_status run_stage(mm_state* s, StageParams<T>& p, bool reduce) {
+    const int nb = (int)((s->N + 255) / 256);
+    if (reduce) {
+        MM_TRY(ensure_partials(s, nb));
+        p.partials = s->partials;
+    } else {
+        p.partials = nullptr;
+    }
+    int nblocks = 0;
+    s->timer.begin(s->st, "stage_llg");
+    launch_stage<T>(p, s->st, &nblocks);
+    s->timer.end(s->st);
+    MM_LAUNCHED();
+    if (reduce) {
+        s->timer.begin(s->st, "finalize_reduce");
+        launch_finalize(s->partials, nblocks, s->scalars, s->st);
+        s->timer.end(s->st);
+        MM_LAUNCHED();
+    }
+    return MM_OK;
+}
+
+mm_status read_scalars(mm_state* s) {
+    MM_CUDA(cudaMemcpyAsync(s->h_scalars, s->scalars, sizeof(double) * kNPart, cudaMemcpyDeviceToHost, s->st));
+    MM_CUDA(cudaStreamSynchronize(s->st));
+    return MM_OK;
+}
+
+template <typename T>
+mm_status heff_impl(mm_state* s, const void* m, void* h_out, double* E_out, double t, double* torque_out) {
+    MM_TRY(ready_for_fields(s));
+    if (!m && !s->have_m) return fail(MM_ENOTSETUP, "no magnetisation: call mm_set_m or pass m");
+    const void* mm_ = m ? m : s->m;
+    MM_TRY(run_demag<T>(s, mm_));
+    StageParams<T> p;
+    fill_common<T>(s, p, mm_, t);
+    p.h_out = (T*)h_out;
+    p.want_energy = E_out != nullptr;
+    p.want_torque = torque_out != nullptr;
+    const bool reduce = E_out || torque_out;
+    MM_TRY(run_stage<T>(s, p, reduce));
+    if (reduce) {
+        MM_TRY(read_scalars(s));
+        if (E_out)
+            for (int q = 0; q < 4; ++q) E_out[q] = s->h_scalars[R_EDEM + q];
+        if (torque_out) *torque_out = s->h_scalars[R_TORQUE];
+    }
+    return MM_OK;
+}
+
+const double kRK4_C[4] = {0.0, 0.5, 0.5, 1.0};
+
+template <typename T> mm_status rk4_impl(mm_state* s, double dt, double t) {
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double anext[3] = {0.5, 0.5, 1.0};
+    void* in[4] = {s->m, s->mA, s->mB, s->mA};
+    void* out[4] = {s->mA, s->mB, s->mA, s->m};
+    for (int st = 0; st < 4; ++st) {
+        MM_TRY(run_demag<T>(s, in[st]));
+        StageParams<T> p;
+        fill_common<T>(s, p, in[st], t + kRK4_C[st] * dt);
+        p.dt = dt;
+        p.next = (T*)out[st];
+        if (st < 3) {
+            p.acc_in = st == 0 ? nullptr : (const T*)s->acc;
+            p.acc_out = (T*)s->acc;
+            p.acc_b = b[st];
+            p.ck = anext[st];
+        } else {
+            p.kin[0] = (const T*)s->acc;
+            p.kc[0] = 1.0;
+            p.nk = 1;
+            p.ck = b[3];
+            p.renorm = 1;
+        }
+        MM_TRY(run_stage<T>(s, p, false));
+    }
+    s->fsal = false;
+    return MM_OK;
+}
+
+// Dormand-Prince 5(4) tableau (Dormand & Prince 1980)
+const double kDP_C[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+const double kDP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+const double kDP_B5[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
+const double kDP_B4[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0,
+                          187.0 / 2100.0, 1.0 / 40.0};
+
+mm_status ensure_dp_buffers(mm_state* s) {
+    for (int q = 0; q < 7; ++q)
+        if (!s->K[q]) MM_TRY(dev_alloc(&s->K[q], 3 * s->rsz * (size_t)s->N));
+    return MM_OK;
+}
+
+// k1 = f(m, t) into K[0]; optional torque readback
+template <typename T> mm_status dp_first_stage(mm_state* s, double t, double* torque) {
+    MM_TRY(run_demag<T>(s, s->m));
+    StageParams<T> p;
+    fill_common<T>(s, p, s->m, t);
+    p.k_out = (T*)s->K[0];
+    p.want_torque = torque != nullptr;
+    MM_TRY(run_stage<T>(s, p, torque != nullptr));
+    if (torque) {
+        MM_TRY(read_scalars(s));
+        *torque = s->h_scalars[R_TORQUE];
+        if (s->h_scalars[R_NONFINITE] != 0.0) return fail(MM_ENONFINITE, "non-finite field or torque");
+    }
+    s->fsal = true;
+    return MM_OK;
+}
+
+// one DP45 attempt with step dt; fills err, torque (at y5) and leaves y5 in *y5buf
+template <typename T>
+mm_status dp_attempt(mm_state* s, double t, double dt, double rtol, double* err, double* torque, void** y5buf) {
+    // y2 = m + dt a21 k1
+    const T* k0 = (const T*)s->K[0];
+    launch_combine<T>((const T*)s->m, &k0, &kDP_A[1][0], 1, dt, (T*)s->mA, s->N, s->st);
+    MM_LAUNCHED();
+    void* ybuf[2] = {s->mA, s->mB};
+    int cur = 0;
+    for (int st = 1; st <= 6; ++st) {     // stage st computes K[st] from y_{st+1} (0-based K)
+        void* yin = ybuf[cur];
+        MM_TRY(run_demag<T>(s, yin));
+        StageParams<T> p;
+        fill_common<T>(s, p, yin, t + kDP_C[st] * dt);
+        p.dt = dt;
+        p.k_out = (T*)s->K[st];
+        if (st < 6) {
+            p.next = (T*)ybuf[1 - cur];
+            for (int q = 0; q < st; ++q) { p.kin[q] = (const T*)s->K[q]; p.kc[q] = kDP_A[st + 1][q]; }
+            p.nk = st;
+            p.ck = kDP_A[st + 1][st];
+            MM_TRY(run_stage<T>(s, p, false));
+            cur = 1 - cur;
+        } else {
+            // last stage: k7 = f(y7), error estimate, torque at y7
+            for (int q = 0; q < 6; ++q) { p.kin[q] = (const T*)s->K[q]; p.eb[q] = kDP_B5[q] - kDP_B4[q]; }
+            p.nk = 6;
+            p.eb_k = kDP_B5[6] - kDP_B4[6];
+            p.want_err = 1;
+            p.rtol = rtol;
+            p.atol = rtol;
+            p.want_torque = 1;
+            MM_TRY(run_stage<T>(s, p, true));
+            *y5buf = yin;
+        }
+    }
+    MM_TRY(read_scalars(s));
+    *err = s->h_scalars[R_ERR];
+    *torque = s->h_scalars[R_TORQUE];
+    if (s->h_scalars[R_NONFINITE] != 0.0 || !std::isfinite(*err))
+        return fail(MM_ENONFINITE, "non-finite values in a DP45 stage");
+    return MM_OK;
+}
+
+double dp_factor(double err) {
+    if (err == 0.0) return 5.0;
+    return std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+}
+
+template <typename T>
+mm_status dp_step(mm_state* s, double* dt_inout, double rtol, double* t_inout, double* torque_out) {
+    MM_TRY(ensure_dp_buffers(s));
+    if (!s->fsal) MM_TRY(dp_first_stage<T>(s, *t_inout, nullptr));
+    double dt = *dt_inout;
+    for (;;) {
+        if (!(dt >= 1e-22)) return fail(MM_ESTEP, "DP45 step size underflow (dt = %g s)", dt);
+        double err = 0, tq = 0;
+        void* y5 = nullptr;
+        MM_TRY(dp_attempt<T>(s, *t_inout, dt, rtol, &err, &tq, &y5));
+        const double f = dp_factor(err);
+        if (err <= 1.0) {
+            launch_renorm_copy<T>((const T*)y5, (T*)s->m, s->N, s->st);
+            MM_LAUNCHED();
+            std::swap(s->K[0], s->K[6]);    // first same as last
+            s->fsal = true;
+            *t_inout += dt;
+            *dt_inout = dt * f;
+            if (torque_out) *torque_out = tq;
+            return MM_OK;
+        }
+        dt *= f;
+    }
+}
+
+}  // namespace
+
+// ================================================================= ABI ====
+extern "C" {
+
+const char* mm_last_error(void) { return g_err.c_str(); }
+
+const char* mm_version(void) { return "libmm 0.1 (sm_103a)"; }
+
+mm_status mm_state_create(const mm_grid* grid, mm_precision precision, void* cuda_stream, mm_state** out) {
+    if (!grid || !out) return fail(MM_EINVAL, "null argument");
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(MM_EINVAL, "grid sizes must be >= 1");
+    if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0)) return fail(MM_EINVAL, "cell sizes must be > 0");
+    if ((double)grid->nx * grid->ny * grid->nz >= 2147483648.0) return fail(MM_EINVAL, "too many cells");
+    if (precision != MM_FP64 && precision != MM_FP32_FIELDS) return fail(MM_EINVAL, "bad precision");
+    const int LX = grid->nx == 1 ? 1 : next_pow2(2 * grid->nx);
+    const int LY = grid->ny == 1 ? 1 : next_pow2(2 * grid->ny);
+    const int LZ = grid->nz == 1 ? 1 : next_pow2(2 * grid->nz);
+    if (LX > kMaxFft || LY > kMaxFft || LZ > kMaxFft)
+        return fail(MM_EINVAL, "padded FFT extent above %d (grid %d x %d x %d)", kMaxFft, grid->nx, grid->ny,
+                    grid->nz);
+    mm_state* s = new (std::nothrow) mm_state();
+    if (!s) return fail(MM_ENOMEM, "host allocation");
+    s->g = *grid;
+    s->prec = precision;
+    s->st = (cudaStream_t)cuda_stream;
+    s->rsz = precision == MM_FP64 ? sizeof(double) : sizeof(float);
+    s->csz = 2 * s->rsz;
+    s->N = (long)grid->nx * grid->ny * grid->nz;
+    const int align = (int)(128 / s->csz);      // 128-byte rows
+    const int KX = LX / 2 + 1;
+    s->d = DemagDims{grid->nx, grid->ny, grid->nz, LX, LY, LZ, KX, (KX + align - 1) / align * align};
+    auto bail = [&](mm_status st) { mm_state_destroy(s); return st; };
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) return bail(fail(MM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    mm_status st = ensure_twiddles(s->device);
+    if (st != MM_OK) return bail(st);
+    const size_t v3 = 3 * s->rsz * (size_t)s->N;
+    const size_t s1 = 3 * s->csz * (size_t)grid->ny * grid->nz * s->d.KXS;
+    const size_t s2 = LY > 1 ? 3 * s->csz * (size_t)grid->nz * LY * s->d.KXS : 0;
+    void** bufs[5] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd};
+    for (void** b : bufs)
+        if ((st = dev_alloc(b, v3)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&s->S1, s1)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&s->S2, s2)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&s->scalars), sizeof(double) * kNPart)) != MM_OK) return bail(st);
+    e = cudaMallocHost(reinterpret_cast<void**>(&s->h_scalars), sizeof(double) * kNPart);
+    if (e != cudaSuccess) return bail(fail(MM_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    // spectrum padding columns are never written by the passes; keep them defined
+    e = cudaMemsetAsync(s->S1, 0, s1, s->st);
+    if (e == cudaSuccess && s2) e = cudaMemsetAsync(s->S2, 0, s2, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->hd, 0, v3, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return bail(fail(MM_ECUDA, "initialising buffers: %s", cudaGetErrorString(e)));
+    *out = s;
+    return MM_OK;
+}
+
+void mm_state_destroy(mm_state* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->st);
+    void** bufs[] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd, &s->S1, &s->S2, &s->tens, &s->Ms_cell,
+                     &s->A_cell, &s->Ku_cell, &s->alpha_cell, &s->axis_tab, reinterpret_cast<void**>(&s->grain),
+                     &s->zw, reinterpret_cast<void**>(&s->partials), reinterpret_cast<void**>(&s->scalars)};
+    for (void** b : bufs) dev_free(*b);
+    for (int q = 0; q < 7; ++q) dev_free(s->K[q]);
+    if (s->h_scalars) cudaFreeHost(s->h_scalars);
+    s->timer.destroy();
+    delete s;
+}
+
+mm_status mm_set_material(mm_state* s, const mm_material* mat, int ptrs_on_device) {
+    MM_TRY(check_state(s));
+    if (!mat) return fail(MM_EINVAL, "null material");
+    if (!(mat->Ms >= 0) || !(mat->A >= 0) || !(mat->alpha >= 0) || !std::isfinite(mat->Ku1))
+        return fail(MM_EINVAL, "material scalars must satisfy Ms >= 0, A >= 0, alpha >= 0, finite Ku1");
+    if (mat->grain_id && (mat->ngrains < 1 || mat->ngrains > 256 || !mat->ku_axis_table))
+        return fail(MM_EINVAL, "grain_id needs ku_axis_table and 1 <= ngrains <= 256");
+    MM_TRY(set_device(s));
+    s->Ms = mat->Ms; s->A = mat->A; s->Ku = mat->Ku1; s->alpha = mat->alpha;
+    for (int q = 0; q < 3; ++q) s->axis[q] = mat->ku_axis[q];
+    MM_TRY(upload_real(s, mat->Ms_cell, s->N, ptrs_on_device, &s->Ms_cell));
+    MM_TRY(upload_real(s, mat->A_cell, s->N, ptrs_on_device, &s->A_cell));
+    MM_TRY(upload_real(s, mat->Ku1_cell, s->N, ptrs_on_device, &s->Ku_cell));
+    MM_TRY(upload_real(s, mat->alpha_cell, s->N, ptrs_on_device, &s->alpha_cell));
+    MM_TRY(upload_real(s, mat->grain_id ? mat->ku_axis_table : nullptr, 3L * mat->ngrains, ptrs_on_device,
+                       &s->axis_tab));
+    dev_free(reinterpret_cast<void*&>(s->grain));
+    if (mat->grain_id) {
+        MM_TRY(dev_alloc(reinterpret_cast<void**>(&s->grain), (size_t)s->N));
+        MM_CUDA(cudaMemcpyAsync(s->grain, mat->grain_id, (size_t)s->N,
+                                ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+        MM_CUDA(cudaStreamSynchronize(s->st));
+    }
+    s->have_mat = true;
+    s->fsal = false;
+    return MM_OK;
+}
+
+mm_status mm_set_m(mm_state* s, const void* m, int on_device) {
+    MM_TRY(check_state(s));
+    if (!m) return fail(MM_EINVAL, "null m");
+    MM_TRY(set_device(s));
+    MM_CUDA(cudaMemcpyAsync(s->m, m, 3 * s->rsz * (size_t)s->N,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    s->have_m = true;
+    s->fsal = false;
+    return MM_OK;
+}
+
+mm_status mm_get_m(const mm_state* s, void* m_out, int on_device) {
+    MM_TRY(check_state(s));
+    if (!m_out) return fail(MM_EINVAL, "null m_out");
+    MM_TRY(set_device(s));
+    MM_CUDA(cudaMemcpyAsync(m_out, s->m, 3 * s->rsz * (size_t)s->N,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    if (!on_device) MM_CUDA(cudaStreamSynchronize(s->st));
+    return MM_OK;
+}
+
+mm_status mm_set_zeeman(mm_state* s, const double h_const[3], mm_field_fn fn, void* user, const double* weight,
+                        int on_device) {
+    MM_TRY(check_state(s));
+    MM_TRY(set_device(s));
+    for (int q = 0; q < 3; ++q) s->h0[q] = h_const ? h_const[q] : 0.0;
+    s->fn = fn;
+    s->user = user;
+    MM_TRY(upload_real(s, weight, s->N, on_device, &s->zw));
+    s->fsal = false;
+    return MM_OK;
+}
+
+mm_status mm_demag_setup(mm_state* s, int p_newell) {
+    MM_TRY(check_state(s));
+    MM_TRY(set_device(s));
+    const int n[3] = {s->g.nx, s->g.ny, s->g.nz};
+    const double dd[3] = {s->g.dx, s->g.dy, s->g.dz};
+    const int P[3] = {s->d.LX, s->d.LY, s->d.LZ};
+    std::vector<double> spec;
+    tensor_spectrum(n, dd, p_newell, P, s->d.KXS, spec);
+    const long cnt = (long)spec.size();
+    dev_free(s->tens);
+    MM_TRY(dev_alloc(&s->tens, s->rsz * (size_t)cnt));
+    if (s->prec == MM_FP64) {
+        MM_CUDA(cudaMemcpyAsync(s->tens, spec.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, s->st));
+    } else {
+        std::vector<float> f(cnt);
+        for (long i = 0; i < cnt; ++i) f[i] = (float)spec[i];
+        MM_CUDA(cudaMemcpyAsync(s->tens, f.data(), sizeof(float) * cnt, cudaMemcpyHostToDevice, s->st));
+        MM_CUDA(cudaStreamSynchronize(s->st));
+    }
+    MM_CUDA(cudaStreamSynchronize(s->st));
+    s->demag_ready = true;
+    s->demag_off = false;
+    s->fsal = false;
+    return MM_OK;
+}
+
+mm_status mm_demag_disable(mm_state* s) {
+    MM_TRY(check_state(s));
+    s->demag_off = true;
+    s->fsal = false;
+    return MM_OK;
+}
+
+mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], double t, double* torque_out) {
+    MM_TRY(check_state(s));
+    MM_TRY(set_device(s));
+    return s->prec == MM_FP64 ? heff_impl<double>(s, m, h_out, E_out, t, torque_out)
+                              : heff_impl<float>(s, m, h_out, E_out, t, torque_out);
+}
+
+mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rtol, double* t_inout) {
+    MM_TRY(check_state(s));
+    if (!dt_inout || !t_inout) return fail(MM_EINVAL, "null dt or t");
+    if (!(*dt_inout > 0) || !std::isfinite(*dt_inout)) return fail(MM_EINVAL, "dt must be > 0");
+    MM_TRY(ready_for_fields(s));
+    if (!s->have_m) return fail(MM_ENOTSETUP, "mm_set_m has not been called");
+    MM_TRY(set_device(s));
+    if (method == MM_RK4) {
+        MM_TRY(s->prec == MM_FP64 ? rk4_impl<double>(s, *dt_inout, *t_inout) : rk4_impl<float>(s, *dt_inout, *t_inout));
+        *t_inout += *dt_inout;
+        return MM_OK;
+    }
+    if (method == MM_DP45) {
+        if (!(rtol > 0)) return fail(MM_EINVAL, "rtol must be > 0");
+        return s->prec == MM_FP64 ? dp_step<double>(s, dt_inout, rtol, t_inout, nullptr)
+                                  : dp_step<float>(s, dt_inout, rtol, t_inout, nullptr);
+    }
+    return fail(MM_EINVAL, "unknown method %d", (int)method);
+}
+
+mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* dt_inout, double* t_inout,
+                   int* steps_out, double* torque_out) {
+    MM_TRY(check_state(s));
+    if (!(tol > 0) || max_steps < 0 || !(rtol > 0)) return fail(MM_EINVAL, "bad tol, rtol or max_steps");
+    MM_TRY(ready_for_fields(s));
+    if (!s->have_m) return fail(MM_ENOTSETUP, "mm_set_m has not been called");
+    MM_TRY(set_device(s));
+    double dt = (dt_inout && *dt_inout > 0) ? *dt_inout : 1e-13;
+    double t = t_inout ? *t_inout : 0.0;
+    double tq = 0.0;
+    MM_TRY(ensure_dp_buffers(s));
+    MM_TRY(s->prec == MM_FP64 ? dp_first_stage<double>(s, t, &tq) : dp_first_stage<float>(s, t, &tq));
+    int steps = 0;
+    mm_status st = MM_OK;
+    while (tq >= tol && steps < max_steps) {
+        st = s->prec == MM_FP64 ? dp_step<double>(s, &dt, rtol, &t, &tq) : dp_step<float>(s, &dt, rtol, &t, &tq);
+        if (st != MM_OK) break;
+        ++steps;
+    }
+    if (dt_inout) *dt_inout = dt;
+    if (t_inout) *t_inout = t;
+    if (steps_out) *steps_out = steps;
+    if (torque_out) *torque_out = tq;
+    if (st != MM_OK) return st;
+    if (tq >= tol) return fail(MM_ENOTCONVERGED, "relax: torque %g >= %g after %d steps", tq, tol, steps);
+    return MM_OK;
+}
+
+mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out) {
+    if (!grid || !out) return fail(MM_EINVAL, "null argument");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return fail(MM_EINVAL, "bad grid");
+    const int n[3] = {grid->nx, grid->ny, grid->nz};
+    const double dd[3] = {grid->dx, grid->dy, grid->dz};
+    tensor_full_offsets(n, dd, p_newell, out);
+    return MM_OK;
+}
+
+mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out) {
+    if (!grid || !out) return fail(MM_EINVAL, "null argument");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return fail(MM_EINVAL, "bad grid");
+    const int n[3] = {grid->nx, grid->ny, grid->nz};
+    const double dd[3] = {grid->dx, grid->dy, grid->dz};
+    const int P[3] = {grid->nx == 1 ? 1 : next_pow2(2 * grid->nx), grid->ny == 1 ? 1 : next_pow2(2 * grid->ny),
+                      grid->nz == 1 ? 1 : next_pow2(2 * grid->nz)};
+    if (P[0] > kMaxFft || P[1] > kMaxFft || P[2] > kMaxFft) return fail(MM_EINVAL, "padded extent too large");
+    std::vector<double> spec;
+    tensor_spectrum(n, dd, p_newell, P, P[0] / 2 + 1, spec);
+    std::memcpy(out, spec.data(), sizeof(double) * spec.size());
+    return MM_OK;
+}
+
+mm_status mm_state_info(const mm_state* s, int out[5]) {
+    MM_TRY(check_state(s));
+    if (!out) return fail(MM_EINVAL, "null out");
+    out[0] = s->d.LX; out[1] = s->d.LY; out[2] = s->d.LZ; out[3] = s->d.KX; out[4] = s->d.KXS;
+    return MM_OK;
+}
+
+mm_status mm_profile_enable(mm_state* s, int on) {
+    MM_TRY(check_state(s));
+    if (on) {
+        cudaStreamSynchronize(s->st);
+        s->timer.reset();
+    }
+    s->timer.on = on != 0;
+    return MM_OK;
+}
+
+int mm_profile_read(mm_state* s, const char** names, int* counts, double* ms, int max) {
+    if (!s) return -1;
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) return -1;
+    const int nn = (int)s->timer.names.size();
+    std::vector<double> tot(nn, 0.0);
+    std::vector<int> cnt(nn, 0);
+    for (const auto& r : s->timer.recs) {
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, r.a, r.b) == cudaSuccess) {
+            tot[r.name] += f;
+            cnt[r.name] += 1;
+        }
+    }
+    const int k = std::min(nn, max);
+    for (int i = 0; i < k; ++i) {
+        if (names) names[i] = s->timer.names[i].c_str();
+        if (counts) counts[i] = cnt[i];
+        if (ms) ms[i] = tot[i];
+    }
+    return nn;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+"""GPU parity of the integrators: RK4 trajectories (m and energies every
+step) on the 32x32x4 plain workload, Dormand-Prince 5(4) steps (same
+accepted step sizes), relaxation, and the invariants |m| = 1 and energy
+decay under damping."""
+import numpy as np
+import pytest
+
+from gpu_util import FP32_TOL, oracle_problem, rel, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rk4_trajectory_fp64_matches_oracle_every_step():
+    from oracle.llg import rk4_step
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.plain_fp64()
+    s = setup_workload(w, "fp64")
+    prob = oracle_problem(w)
+    m = w.m0.copy()
+    t = 0.0
+    worst_m = worst_E = 0.0
+    for step in range(w.steps):
+        t_new, _ = s.step(w.dt, t, "rk4")
+        m = rk4_step(prob, m, t, w.dt)
+        t = t_new
+        if step % 10 == 9 or step == w.steps - 1:
+            mg = from_soa(to_host(s.get_m()))
+            worst_m = max(worst_m, rel(mg, m))
+            _, E = s.heff(t=t, energies=True)
+            Er = prob.energies(m, t)
+            worst_E = max(worst_E, abs(sum(E) - sum(Er)) / abs(sum(Er)))
+    # 200 steps accumulate the tensor's rounding noise (about 2e-11 per field
+    # evaluation on this grid); the bound below is 5x the per-evaluation bound
+    assert worst_m < 5e-10, worst_m
+    assert worst_E < 5e-10, worst_E
+    assert np.max(np.abs(np.linalg.norm(mg, axis=-1) - 1.0)) < 1e-14
+    s.close()
+
+
+def test_rk4_fp32_fields_error_vs_fp64_oracle():
+    from oracle.llg import rk4_step
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.plain_fp64()
+    s = setup_workload(w, "fp32")
+    prob = oracle_problem(w)
+    m = w.m0.copy()
+    t = 0.0
+    for step in range(20):
+        t_new, _ = s.step(w.dt, t, "rk4")
+        m = rk4_step(prob, m, t, w.dt)
+        t = t_new
+    mg = from_soa(to_host(s.get_m()))
+    # state error after 20 FP32 steps (each field evaluation <= 1e-5)
+    assert rel(mg, m) < 20 * FP32_TOL
+    s.close()
+
+
+def test_energy_decays_and_norm_kept_on_gpu():
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.bulk(crop=((0, 32), (0, 32), (0, 8)))
+    for precision in ("fp64", "fp32"):
+        s = setup_workload(w, precision)
+        t = 0.0
+        _, E0 = s.heff(t=t, energies=True)
+        prev = sum(E0)
+        for _ in range(30):
+            t, _ = s.step(w.dt, t, "rk4")
+            _, E = s.heff(t=t, energies=True)
+            assert sum(E) <= prev + (1e-12 if precision == "fp64" else 1e-6) * abs(prev)
+            prev = sum(E)
+        m = from_soa(to_host(s.get_m()))
+        assert np.max(np.abs(np.linalg.norm(m, axis=-1) - 1.0)) < (1e-14 if precision == "fp64" else 1e-6)
+        s.close()
+
+
+def test_dp45_steps_match_oracle():
+    from oracle.llg import dp45_attempt, dp45_factor, normalize
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.thin_film(n=(64, 32, 1))
+    s = setup_workload(w, "fp64")
+    prob = oracle_problem(w)
+    rtol = w.extra["rtol"]
+    m = w.m0.copy()
+    t, dt = 0.0, 1e-13
+    k1 = prob.rhs(m, t)
+    tg, dtg = 0.0, 1e-13
+    for step in range(12):
+        while True:
+            y5, k7, _, err = dp45_attempt(prob, m, t, dt, k1, rtol)
+            f = dp45_factor(err)
+            if err <= 1.0:
+                t += dt
+                m = normalize(y5)
+                k1 = k7
+                dt *= f
+                break
+            dt *= f
+        tg, dtg = s.step(dtg, tg, "dp45", rtol)
+        assert abs(tg - t) <= 1e-9 * t and abs(dtg - dt) <= 1e-6 * dt, (tg, t, dtg, dt)
+    mg = from_soa(to_host(s.get_m()))
+    assert rel(mg, m) < 1e-9
+    s.close()
+
+
+def test_relax_matches_oracle():
+    from oracle.llg import relax
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import Workload, from_soa
+    rng = np.random.default_rng(9)
+    n = (16, 8, 2)
+    m0 = rng.normal(size=n + (3,))
+    m0 /= np.linalg.norm(m0, axis=-1, keepdims=True)
+    w = Workload("relax 16x8x2", n, (3e-9, 3e-9, 3e-9), Ms=8e5, A=1.3e-11, alpha=1.0, m0=m0)
+    s = setup_workload(w, "fp64")
+    steps, tq, t, _ = s.relax(tol=1e-3, max_steps=5000, rtol=1e-5)
+    prob = oracle_problem(w)
+    mr, steps_r, tq_r, t_r = relax(prob, m0, tol=1e-3, max_steps=5000)
+    assert steps == steps_r
+    assert tq < 1e-3 and abs(tq - tq_r) < 1e-6 * tq_r
+    assert rel(from_soa(to_host(s.get_m())), mr) < 1e-8
+    s.close()
