@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark: cell-updates per second per Runge-Kutta stage on the bulk
+workload (256 x 256 x 64 cells of 2 nm, 64 Voronoi grains, FP32 fields), the
+plain FP64 path beside it, and the CPU oracle as baseline.
+
+One step = one classic RK4 step = four full stages of the hot path (demag by
+the five FFT passes, local terms + LLG + RK combination, renormalisation).
+value = cells x 4 x steps / device time, summed over ranks (replicas: every
+rank solves its own copy; no data-path collective).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage at 256x256x64 (FP32 fields)"
+UNIT = "cell-updates/s"
+WORKLOAD = "bulk 256x256x64 cells of 2 nm, Ms 1e6 A/m, A 1.5e-11 J/m, Ku1 4e5 J/m^3 on 64 Voronoi grains, alpha 0.1, RK4 dt 5e-14 s"
+STAGES_PER_STEP = 4
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, see the design doc
+
+
+# ----------------------------------------------------------------- models --
+def padded(n):
+    out = []
+    for v in n:
+        p = 1
+        while p < 2 * v:
+            p *= 2
+        out.append(1 if v == 1 else p)
+    return out
+
+
+def kernel_bytes(n, s, grains=True, ms_cell=False):
+    """Algorithmic HBM bytes per launch of each kernel (data the kernel must
+    read or write once), for real size s (4 FP32, 8 FP64)."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    LX, LY, LZ = padded(n)
+    KX = LX // 2 + 1
+    cs = 2 * s
+    S1 = 3 * nz * ny * KX * cs
+    S2 = 3 * nz * LY * KX * cs
+    tens = 6 * (LZ // 2 + 1) * (LY // 2 + 1) * KX * s
+    v3 = 3 * N * s
+    g = N if grains else 0
+    mc = N * s if ms_cell else 0
+    # stage kernel of RK4, averaged over the four stages:
+    # reads m_s, h_demag, m_n (all stages), acc (stages 2-4), grain ids; writes acc (1-3), next (all)
+    stage = (4 * (3 * v3 + g + mc) + 3 * v3 + 3 * v3 + 4 * v3) / 4.0
+    return {
+        "p1_x_forward": v3 + mc + S1,
+        "p2_y_forward": S1 + S2,
+        "p3_z_conv": 2 * S2 + tens,
+        "p4_y_inverse": S2 + S1,
+        "p5_x_inverse": S1 + v3,
+        "stage_llg": stage,
+    }
+
+
+def model_stage_bytes(n, s):
+    """The per-stage traffic model of the design notes (one HBM read+write per
+    FFT axis pass, tensor once, 73 B/cell of local/RK traffic at FP32; scaled
+    with the real size)."""
+    nx, ny, nz = n
+    LX, LY, LZ = padded(n)
+    KX = LX // 2 + 1
+    cs = 2 * s
+    fft = 4 * 3 * cs * KX * ny * nz + 4 * 3 * cs * KX * LY * nz
+    tens = 6 * s * KX * (ny + 1) * (nz + 1)
+    local = (73.0 / 4.0) * s * nx * ny * nz
+    return fft + tens + local
+
+
+def stage_flops(n):
+    """Floating-point operations of one stage (5 L log2 L per complex line
+    transform, half for a real line, 30 per k-point for the 3x3 multiply,
+    about 150 per cell for local terms, LLG and the RK combination)."""
+    nx, ny, nz = n
+    LX, LY, LZ = padded(n)
+    KX = LX // 2 + 1
+    lg = lambda L: math.log2(L) if L > 1 else 0.0
+    f = 2 * 3 * ny * nz * 2.5 * LX * lg(LX)                 # P1 + P5
+    f += 2 * 3 * nz * KX * 5 * LY * lg(LY)                  # P2 + P4
+    f += KX * LY * 3 * 2 * 5 * LZ * lg(LZ) + KX * LY * LZ * 30   # P3
+    f += 150 * nx * ny * nz
+    return f
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, gpu_indices):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    idx = int(parts[0])
+                except ValueError:
+                    continue
+                if idx in gpu_indices:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- CPU baseline --
+def _oracle_sample(result_path, n_stages, crop):
+    """Time RK stages of the unmodified oracle on the bulk workload (or a crop
+    of the same construction).  Runs in a spawned process."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle.llg import Problem
+    from paper_2302_08843_gb300 import workloads as W
+    w = W.bulk(crop=crop)
+    prob = Problem(w.n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, Ku1=w.Ku1, ku_axis=w.ku_axis_cells(),
+                   h_ext=w.h_ext)
+    m = w.m0
+    t0 = time.perf_counter()
+    for s in range(n_stages):
+        k = prob.rhs(m, s * w.dt)
+        m = m + 0.5 * w.dt * k
+    el = time.perf_counter() - t0
+    json.dump({"seconds": el, "stages": n_stages, "cells": w.ncells, "n": list(w.n)}, open(result_path, "w"))
+
+
+def start_cpu_baseline(n_stages=1, crop=None):
+    ctx = mp.get_context("spawn")
+    path = tempfile.NamedTemporaryFile(suffix=".json", delete=False).name
+    p = ctx.Process(target=_oracle_sample, args=(path, n_stages, crop))
+    p.start()
+    return p, path
+
+
+def finish_cpu_baseline(p, path, sample_desc):
+    p.join()
+    try:
+        r = json.load(open(path))
+    except Exception:
+        return None
+    finally:
+        try:
+            os.unlink(path)
+        except OSError:
+            pass
+    return {"value": r["cells"] * r["stages"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample_desc % r}
+
+
+# ------------------------------------------------------------------ ours --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def traffic_for(kernel, precision):
+    """ncu DRAM bytes per launch from the committed profile summary, or None
+    when the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    e = d.get("kernels", {}).get(precision, {}).get(kernel)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+def source_hash():
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2302_08843_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def time_precision(torch, w, precision, steps, warmup, peaks):
+    from paper_2302_08843_gb300.binding import setup_workload
+    stream = torch.cuda.current_stream()
+    s = setup_workload(w, precision, stream=stream)
+    t = 0.0
+    for _ in range(warmup):
+        t, _ = s.step(w.dt, t, "rk4")
+    torch.cuda.synchronize()
+    s.profile_enable(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        t, _ = s.step(w.dt, t, "rk4")
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    prof = s.profile_read()
+    s.profile_enable(False)
+    return s, ms, prof
+
+
+def e2e_measure(torch, s, w, steps, warmup):
+    """Same metric through the C ABI with host buffers: every step copies m in
+    from pinned host memory (mm_set_m), runs one RK4 step (mm_llg_step) and
+    reads m back to pinned host memory (mm_get_m)."""
+    from paper_2302_08843_gb300.workloads import to_soa
+    mh = torch.from_numpy(to_soa(w.m0).astype("float32" if s.dtype == torch.float32 else "float64")).pin_memory()
+    out = torch.empty_like(mh).pin_memory()
+    t = 0.0
+    for _ in range(warmup):
+        s.set_m(mh)
+        t, _ = s.step(w.dt, t, "rk4")
+        s.get_m_host(out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_m(mh)
+        t, _ = s.step(w.dt, t, "rk4")
+        s.get_m_host(out)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    nbytes = mh.numel() * mh.element_size()
+    return el, nbytes
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    from paper_2302_08843_gb300 import workloads as W
+    w = W.bulk()
+    w.steps = args.steps
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = start_cpu_baseline(n_stages=1)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(v):
+        if dist is None:
+            return v
+        tt = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    results = {}
+    clocks = None
+    for precision in ("fp32", "fp64"):
+        steps = args.steps if precision == "fp32" else max(2, args.steps // 10)
+        barrier()
+        sampler = ClockSampler() if (rank == 0 and precision == "fp32") else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.5)
+        s, ms, prof = time_precision(torch, w, precision, steps, args.warmup, peaks)
+        barrier()
+        if sampler:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            idx = [int(x) for x in vis.split(",")] if vis and all(x.strip().isdigit() for x in vis.split(",")) \
+                else list(range(ws))
+            clocks = sampler.stop(set(idx[:ws]))
+        ms_max = allmax(ms)
+        el_e2e = nbytes = None
+        if precision == "fp32":
+            el_e2e, nbytes = e2e_measure(torch, s, w, max(3, steps // 5), 2)
+            el_e2e = allmax(el_e2e)
+        results[precision] = dict(ms=ms_max, steps=steps, prof=prof, e2e=(el_e2e, nbytes, max(3, steps // 5)))
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    N = w.ncells
+    r32 = results["fp32"]
+    value = ws * N * STAGES_PER_STEP * r32["steps"] / (r32["ms"] / 1e3)
+    ms_step = r32["ms"] / r32["steps"]
+
+    def roofline_info(prof, s_bytes, precision, steps):
+        kb = kernel_bytes(w.n, s_bytes, grains=True)
+        total = sum(v[1] for v in prof.values())
+        kernels = {}
+        for name, (cnt, tms) in prof.items():
+            avg = tms / max(cnt, 1)
+            ent = {"launches": cnt, "total_ms": round(tms, 4), "share": round(tms / total, 4),
+                   "avg_us": round(avg * 1e3, 2)}
+            if name in kb:
+                ach = kb[name] / (avg / 1e3) / 1e9
+                ent.update({"algorithmic_bytes": int(kb[name]), "achieved_gbs": round(ach, 1),
+                            "frac_of_measured_hbm": round(ach / hbm_peak, 4)})
+            kernels[name] = ent
+        dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+        return kernels, dom
+
+    kernels32, dom = roofline_info(r32["prof"], 4, "fp32", r32["steps"])
+    kd = kernels32[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kd.get("achieved_gbs"), "peak": hbm_peak, "unit": "GB/s",
+            "frac": kd.get("frac_of_measured_hbm"), "traffic": traffic_for(dom, "fp32"),
+            "peak_source": peak_src + " hbm_gbs (copy)"}
+    launches = sum(v[0] for v in r32["prof"].values())
+    stage_ms = ms_step / STAGES_PER_STEP
+    model_b = model_stage_bytes(w.n, 4)
+    ach_stage = model_b / (stage_ms / 1e3) / 1e9
+    kern_sum = sum(kernel_bytes(w.n, 4).values()) * 1.0
+    stage_roof = {"model_bytes_per_stage": int(model_b), "ms_per_stage": round(stage_ms, 4),
+                  "achieved_gbs": round(ach_stage, 1), "frac": round(ach_stage / hbm_peak, 4),
+                  "kernel_bytes_per_stage": int(kern_sum)}
+    r64 = results["fp64"]
+    v64 = ws * N * STAGES_PER_STEP * r64["steps"] / (r64["ms"] / 1e3)
+    fl = stage_flops(w.n)
+    st64 = r64["ms"] / r64["steps"] / STAGES_PER_STEP
+    kernels64, dom64 = roofline_info(r64["prof"], 8, "fp64", r64["steps"])
+    fp64 = {"value": v64, "unit": UNIT, "ms_per_step": round(r64["ms"] / r64["steps"], 4), "steps": r64["steps"],
+            "roofline": {"bound": "alu", "achieved": round(fl / (st64 / 1e3) / 1e12, 4),
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": round(fl / (st64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                         "flops_per_stage": int(fl)},
+            "kernels": kernels64, "dominant": dom64}
+    el, nbytes, e2e_steps = r32["e2e"]
+    e2e = {"value": ws * N * STAGES_PER_STEP * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": r32["steps"],
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "cells": N, "padded_fft": padded(w.n),
+                      "stages_per_step": STAGES_PER_STEP, "parallelism": "replicas x%d" % ws,
+                      "l2": "per-stage working set ~0.7 GB > 129 MB L2, no flush"},
+           "roofline": roof, "stage_roofline": stage_roof, "kernels": kernels32,
+           "gpu_launches": launches, "e2e": e2e, "fp64": fp64, "clocks": clocks}
+    if cpu is not None:
+        out["cpu_baseline"] = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stage of the FP64 oracle on the "
+                                                  "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference --
+def run_reference(args):
+    """The oracle (the method written plainly in FP64 NumPy) as the reference
+    arm, on the host cores.  Each step is one RK stage of the bulk workload's
+    construction on a crop sized so that the whole run stays within a few
+    minutes."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    total = args.steps + args.warmup
+    # oracle stage cost per cell is roughly flat; pick the largest crop with
+    # (steps + warmup) stages <= ~120 s on one core (about 6 us per cell-stage)
+    crops = [((0, 256), (0, 256), (0, 64)), ((0, 128), (0, 128), (0, 32)), ((0, 64), (0, 64), (0, 16)),
+             ((0, 32), (0, 32), (0, 8))]
+    crop = crops[-1]
+    for c in crops:
+        cells = (c[0][1] - c[0][0]) * (c[1][1] - c[1][0]) * (c[2][1] - c[2][0])
+        if cells * total * 6e-6 <= 120.0:
+            crop = c
+            break
+    sys.path.insert(0, ROOT)
+    from oracle.llg import Problem
+    from paper_2302_08843_gb300 import workloads as W
+    w = W.bulk(crop=None if crop == crops[0] else crop)
+    prob = Problem(w.n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, Ku1=w.Ku1, ku_axis=w.ku_axis_cells(), h_ext=w.h_ext)
+    m = w.m0
+    for s in range(args.warmup):
+        m = m + 0.5 * w.dt * prob.rhs(m, 0.0)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        m = m + 0.5 * w.dt * prob.rhs(m, 0.0)
+    el = time.perf_counter() - t0
+    value = w.ncells * args.steps / el
+    sample = "one RK stage per step of the FP64 oracle on the %dx%dx%d crop of the bulk workload" % tuple(w.n)
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample_grid": list(w.n)},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

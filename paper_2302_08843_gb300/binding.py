@@ -216,6 +216,14 @@ class State:
         check(lib().mm_get_m(self.h, out.data_ptr(), 1))
         return out
 
+    def get_m_host(self, out):
+        """mm_get_m into a host (ideally pinned) CPU tensor or numpy array; synchronises."""
+        p, dev = _ptr(out)
+        if dev:
+            raise ValueError("get_m_host needs a host buffer")
+        check(lib().mm_get_m(self.h, p, 0))
+        return out
+
     def set_zeeman(self, h=(0.0, 0.0, 0.0), fn=None, weight=None):
         """h: constant (3,) A/m; fn: callable t -> (3,) A/m (overrides h);
         weight: per-cell float64 (nz, ny, nx) numpy array or CUDA tensor."""
