@@ -173,6 +173,32 @@ mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out);
  * doubles (kx fastest), already multiplied by -1/(Px Py Pz). */
 mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out);
 
+/* Demag field without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they need a field -- code capturing a stream into a CUDA graph, where a
+ * cudaMalloc would break the capture, frameworks whose allocator owns all
+ * device memory, or loops that must not stall on the driver's allocator.
+ * It runs the same five FFT passes as mm_heff's demag term on caller buffers:
+ *   m        device, [3][nz][ny][nx] in the precision's real type;
+ *   Ms_cell  device, nx*ny*nz real values, or NULL to use Ms for every cell;
+ *   spectrum device, the layout and values of mm_demag_spectrum_host for this
+ *            grid, converted by the caller to the real type;
+ *   h_out    device, [3][nz][ny][nx] real: the demag field h = -N * (Ms m) in
+ *            every cell (cells with Ms = 0 included, unlike mm_heff).
+ * The intermediate spectra live in one fixed 64 MiB device array inside the
+ * library (held by every GPU that loads it until the process exits); grids
+ * whose spectra need more (about 128x128x32 cells in FP32, half that in FP64)
+ * are rejected with MM_EINVAL and a message giving the size needed.  The first
+ * call on a device looks up that array's address and uploads the FFT twiddle
+ * table (no allocation either); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's data:
+ * calls whose kernels may overlap on the GPU (different streams without
+ * ordering, or several host threads) race on it and must be serialised by the
+ * caller.  Enqueues on cuda_stream (NULL = legacy default stream) and returns
+ * without synchronising. */
+mm_status mm_demag_noalloc(const mm_grid* grid, mm_precision precision, const void* m, const void* Ms_cell,
+                           double Ms, const void* spectrum, void* h_out, void* cuda_stream);
+
 /* Padded FFT extents and the row stride of the x-spectrum of a state
  * (out: Px, Py, Pz, Kx = Px/2+1, Kx_stride). */
 mm_status mm_state_info(const mm_state* s, int out[5]);

@@ -24,7 +24,7 @@ MM_RK4, MM_DP45 = 0, 1
 EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m", "mm_get_m",
            "mm_set_zeeman", "mm_demag_setup", "mm_demag_disable", "mm_heff", "mm_llg_step",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
-           "mm_profile_read", "mm_last_error", "mm_version")
+           "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc")
 
 
 class MMError(RuntimeError):
@@ -82,6 +82,7 @@ def lib():
         "mm_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_char_p), pi, pd, i]),
         "mm_last_error": (ctypes.c_char_p, []),
         "mm_version": (ctypes.c_char_p, []),
+        "mm_demag_noalloc": (i, [ctypes.POINTER(mm_grid), i, vp, vp, d, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -85,5 +85,10 @@ template <typename T> void launch_combine(const T* mn, const T* const* kin, cons
                                           T* out, long N, cudaStream_t st);
 // copy the host-built twiddle table into the FFT kernels' device table (current device)
 cudaError_t upload_twiddles(const double2* w64, const float2* w32);
+// build (once, in static host storage) and upload the twiddle table to device dev, which
+// must be current; a no-op after the first success on that device
+cudaError_t ensure_twiddles_on(int dev);
+// set the thread-local message returned by mm_last_error (fixed storage)
+void set_last_error(const char* msg);
 
 }  // namespace mm

@@ -18,15 +18,13 @@ using namespace mm;
 
 namespace {
 
-thread_local std::string g_err = "no error";
+thread_local char g_err[512] = "no error";   // fixed storage: reporting an error allocates nothing
 
 mm_status fail(mm_status st, const char* fmt, ...) {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
-    g_err = buf;
     return st;
 }
 
@@ -59,21 +57,40 @@ int next_pow2(int v) {
 
 std::mutex g_tw_mu;
 bool g_tw_done[128] = {false};
+double2 g_tw_host64[kMaxFft];    // static host staging: the upload allocates nothing
+float2 g_tw_host32[kMaxFft];
+
+}  // namespace
+
+namespace mm {
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+// Upload the FFT twiddle table to the current device once (no allocation).
+cudaError_t ensure_twiddles_on(int dev) {
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (g_tw_done[dev]) return cudaSuccess;
+    static bool built = false;
+    if (!built) {
+        for (int i = 0; i < kMaxFft; ++i) {
+            double c, sn;
+            twiddle_entry(kMaxFft, i, &c, &sn);
+            g_tw_host64[i] = make_double2(c, sn);
+            g_tw_host32[i] = make_float2((float)c, (float)sn);
+        }
+        built = true;
+    }
+    cudaError_t e = upload_twiddles(g_tw_host64, g_tw_host32);
+    if (e == cudaSuccess) g_tw_done[dev] = true;
+    return e;
+}
+}  // namespace mm
+
+namespace {
 
 mm_status ensure_twiddles(int dev) {
-    std::lock_guard<std::mutex> lk(g_tw_mu);
-    if (dev < 0 || dev >= 128) return fail(MM_EINVAL, "device ordinal %d out of range", dev);
-    if (g_tw_done[dev]) return MM_OK;
-    std::vector<double> re, im;
-    twiddle_table(kMaxFft, re, im);
-    std::vector<double2> w64(kMaxFft);
-    std::vector<float2> w32(kMaxFft);
-    for (int i = 0; i < kMaxFft; ++i) {
-        w64[i] = make_double2(re[i], im[i]);
-        w32[i] = make_float2((float)re[i], (float)im[i]);
-    }
-    MM_CUDA(upload_twiddles(w64.data(), w32.data()));
-    g_tw_done[dev] = true;
+    cudaError_t e = ensure_twiddles_on(dev);
+    if (e != cudaSuccess) return fail(MM_ECUDA, "twiddle upload: %s", cudaGetErrorString(e));
     return MM_OK;
 }
 
@@ -458,7 +475,7 @@ mm_status dp_step(mm_state* s, double* dt_inout, double rtol, double* t_inout, d
 // ================================================================= ABI ====
 extern "C" {
 
-const char* mm_last_error(void) { return g_err.c_str(); }
+const char* mm_last_error(void) { return g_err; }
 
 const char* mm_version(void) { return "libmm 0.1 (sm_103a)"; }
 

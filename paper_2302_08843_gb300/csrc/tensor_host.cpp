@@ -250,6 +250,13 @@ void tensor_spectrum(const int n[3], const double d[3], int p, const int P[3], i
     }
 }
 
+void twiddle_entry(int L, int m, double* re, double* im) {
+    double c, s;
+    unit_root(L, m, &c, &s);
+    *re = c;
+    *im = -s;       // exp(-2 pi i m / L)
+}
+
 void twiddle_table(int L, std::vector<double>& re, std::vector<double>& im) {
     re.resize(L);
     im.resize(L);

@@ -21,5 +21,6 @@ void tensor_spectrum(const int n[3], const double d[3], int p, const int P[3], i
 
 // exp(-2 pi i m / L), m in [0, L), with exact octant symmetry.
 void twiddle_table(int L, std::vector<double>& re, std::vector<double>& im);
+void twiddle_entry(int L, int m, double* re, double* im);
 
 }  // namespace mm
