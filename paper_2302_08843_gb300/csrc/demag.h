@@ -74,10 +74,13 @@ struct StageParams {
     double eb_k;
     double rtol, atol;
     int want_err, want_energy, want_torque;
-    double* partials;            // [gridDim.x][kNPart]
+    double* partials;            // [number of blocks][kNPart]
+    // the coefficients above in the field type (filled by launch_stage)
+    T kcT[7], ckT, dtT, acc_bT;
 };
 
 template <typename T> void launch_stage(const StageParams<T>& p, cudaStream_t st, int* nblocks);
+template <typename T> int stage_blocks(int nx, int ny, int nz);   // blocks launch_stage will use
 void launch_finalize(const double* partials, int nblocks, double* scalars, cudaStream_t st);
 template <typename T> void launch_convert(const double* src, T* dst, long n, cudaStream_t st);
 template <typename T> void launch_renorm_copy(const T* src, T* dst, long N, cudaStream_t st);

@@ -130,16 +130,32 @@ p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
 }
 
 // ------------------------------------------------------------------ P3 ----
+// resident CTAs asked of the register allocator: 1024 (FP32) or 512 (FP64) threads per SM
+template <typename T> constexpr int p3_min_blocks(int threads) {
+    return (sizeof(T) == 4 ? 1024 : 512) / threads > 1 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1;
+}
+
+// Three shared-memory areas, one per component, each the FFT scratch of its
+// component: every global load of the column tile is issued first and parked
+// in its area, then each component is transformed in place, the 3x3 multiply
+// reads and rewrites the areas, and each inverse transform streams its kept
+// half straight to global memory.  Only one component's registers are live at
+// a time, which keeps the kernel at four CTAs per SM.
 template <typename T, int LZ, int B, int G>
-__global__ void __launch_bounds__(B * G * FftLine<T, LZ, -1, (LZ > 1)>::TPL)
+__global__ void __launch_bounds__(B * G * FftLine<T, LZ, -1, (LZ > 1)>::TPL,
+                                  p3_min_blocks<T>(B * G * FftLine<T, LZ, -1, (LZ > 1)>::TPL))
 p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restrict__ tens) {
     using C = typename Cplx<T>::type;
     using FF = FftLine<T, LZ, -1, (LZ > 1)>;
     using FI = FftLine<T, LZ, +1, false>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* s = reinterpret_cast<C*>(smraw);
     constexpr int NL = B * G;
     constexpr int NR = FF::NR, TPL = FF::TPL;
+    constexpr int NIN = LZ == 1 ? 1 : NR / 2;     // registers holding input / kept output
+    C* area[3];
+    area[0] = reinterpret_cast<C*>(smraw);
+    area[1] = area[0] + LZ * NL;
+    area[2] = area[1] + LZ * NL;
     const int tid = threadIdx.x;
     const int line = tid % NL, j = tid / NL;
     const int kl = line % B, g = line / B;
@@ -154,21 +170,30 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
     C* col = S2 + (long)ky * d.KXS + kx;            // element (c, z) at col[c*cstride + z*LY*KXS]
     const long zs = (long)LY * d.KXS;
 
-    C vx[NR], vy[NR], vz[NR];
+    {   // all loads in flight together, parked at this thread's own positions
+        C in[3][NIN];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int z = j + r * TPL;
-        vx[r] = vy[r] = vz[r] = mk<C>(0, 0);
-        if (valid && (LZ == 1 || r < NR / 2) && z < d.nz) {
-            vx[r] = col[z * zs];
-            vy[r] = col[cstride + z * zs];
-            vz[r] = col[2 * cstride + z * zs];
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < NIN; ++r) {
+                const int z = j + r * TPL;
+                in[c][r] = (valid && z < d.nz) ? col[c * cstride + z * zs] : mk<C>(0, 0);
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < NIN; ++r) area[c][(j + r * TPL) * NL + line] = in[c][r];
     }
-    FF::run(vx, s + line, NL, j);
-    FF::run(vy, s + line, NL, j);
-    FF::run(vz, s + line, NL, j);
-
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        C v[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = r < NIN ? area[c][(j + r * TPL) * NL + line] : mk<C>(0, 0);
+        FF::run(v, area[c] + line, NL, j);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) area[c][(j + r * TPL) * NL + line] = v[r];
+    }
+    // h^ = T M^ at this thread's wave numbers (its own positions in the three areas)
     const int KZ2 = LZ / 2 + 1;
     const long tcomp = (long)KZ2 * KY2 * d.KXS;
     const T sy = side ? (T)-1 : (T)1;
@@ -180,29 +205,30 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
         T txx = 0, txy = 0, txz = 0, tyy = 0, tyz = 0, tzz = 0;
         if (valid) {
             const T* tp = tens + ((long)kzf * KY2 + p) * d.KXS + kx;
-            txx = tp[0];
-            txy = sy * tp[tcomp];
-            txz = sz * tp[2 * tcomp];
-            tyy = tp[3 * tcomp];
-            tyz = sy * sz * tp[4 * tcomp];
-            tzz = tp[5 * tcomp];
+            txx = __ldg(tp);
+            txy = sy * __ldg(tp + tcomp);
+            txz = sz * __ldg(tp + 2 * tcomp);
+            tyy = __ldg(tp + 3 * tcomp);
+            tyz = sy * sz * __ldg(tp + 4 * tcomp);
+            tzz = __ldg(tp + 5 * tcomp);
         }
-        const C mx = vx[r], my = vy[r], mz = vz[r];
-        vx[r] = mk<C>(txx * mx.x + txy * my.x + txz * mz.x, txx * mx.y + txy * my.y + txz * mz.y);
-        vy[r] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
-        vz[r] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
+        const int o = (j + r * TPL) * NL + line;
+        const C mx = area[0][o], my = area[1][o], mz = area[2][o];
+        area[0][o] = mk<C>(txx * mx.x + txy * my.x + txz * mz.x, txx * mx.y + txy * my.y + txz * mz.y);
+        area[1][o] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
+        area[2][o] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
     }
-    FI::run(vx, s + line, NL, j);
-    FI::run(vy, s + line, NL, j);
-    FI::run(vz, s + line, NL, j);
-    if (valid) {
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        C v[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int z = j + r * TPL;
-            if ((LZ == 1 || r < NR / 2) && z < d.nz) {
-                col[z * zs] = vx[r];
-                col[cstride + z * zs] = vy[r];
-                col[2 * cstride + z * zs] = vz[r];
+        for (int r = 0; r < NR; ++r) v[r] = area[c][(j + r * TPL) * NL + line];
+        FI::run(v, area[c] + line, NL, j);
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < NIN; ++r) {
+                const int z = j + r * TPL;
+                if (z < d.nz) col[c * cstride + z * zs] = v[r];
             }
         }
     }
@@ -311,7 +337,7 @@ template <typename T, int L> static void launch_p3(const DemagDims& d, typename 
                                                    cudaStream_t st) {
     constexpr int B = b_of<T, L>(), G = g_of<T, L>();
     using C = typename Cplx<T>::type;
-    const size_t sm = (size_t)L * B * G * sizeof(C);
+    const size_t sm = 3 * (size_t)L * B * G * sizeof(C);
     const int kyi = 2 * (d.LY / 2 + 1);
     dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G);
     auto k = p3_z_conv<T, L, B, G>;

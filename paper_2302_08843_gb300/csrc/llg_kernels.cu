@@ -34,126 +34,220 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 template <typename T>
-__device__ __forceinline__ T link_weight(const T* A_cell, T A, T Ai, long nb) {
-    if (!A_cell) return A;
-    const T Aj = A_cell[nb];
-    const T s = Ai + Aj;
-    return s != (T)0 ? (T)2 * Ai * Aj / s : (T)0;
+__device__ __forceinline__ T harmonic(T a, T b) {
+    const T s = a + b;
+    return s != (T)0 ? (T)2 * a * b / s : (T)0;
 }
 
-template <typename T>
+// VEC consecutive cells along x per thread (float4 / double2 loads).
+template <typename T, int VEC> struct Vec;
+template <> struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double* v) {
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        v[0] = q.x; v[1] = q.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double* v) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <typename T> struct Vec<T, 1> {
+    static __device__ __forceinline__ void ld(const T* p, T* v) { v[0] = *p; }
+    static __device__ __forceinline__ void st(T* p, const T* v) { *p = v[0]; }
+};
+
+constexpr int kBX = 64, kBY = 4;   // threads per block: 64 along x, 4 rows of y
+
+// 3-D launch: blockIdx.z = z, blockIdx.y * kBY + threadIdx.y = y,
+// (blockIdx.x * kBX + threadIdx.x) * VEC = first x of the thread's cells.
+// Requires nx % VEC == 0 (all of a thread's cells in one row).
+template <typename T, int VEC>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) {
-    const long N = p.N;
-    const long i = (long)blockIdx.x * kStageThreads + threadIdx.x;
-    double red_torque = 0.0, red_e[4] = {0.0, 0.0, 0.0, 0.0}, red_err = 0.0, red_nf = 0.0;
-    if (i < N) {
-        const int x = (int)(i % p.nx);
-        const long yz = i / p.nx;
-        const int y = (int)(yz % p.ny);
-        const int z = (int)(yz / p.ny);
+    using LV = Vec<T, VEC>;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int N = (int)p.N;
+    const int x0 = (blockIdx.x * kBX + threadIdx.x) * VEC;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    const int z = blockIdx.z;
+    double red_torque = 0.0, red_e0 = 0.0, red_e1 = 0.0, red_e2 = 0.0, red_e3 = 0.0, red_err = 0.0, red_nf = 0.0;
+    if (x0 < nx && y < ny) {
+        const int i = x0 + nx * (y + ny * z);
+        const int sy = nx, sz = nx * ny;
         const T* m = p.m;
-        const T mx = m[i], my = m[N + i], mz = m[2 * N + i];
-        const T Ms = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
-        T hx = 0, hy = 0, hz = 0;
-        T hdx = 0, hdy = 0, hdz = 0, hex = 0, hey = 0, hez = 0, hax = 0, hay = 0, haz = 0;
-        T hzx = 0, hzy = 0, hzz = 0;
-        if (Ms != (T)0) {
-            const T inv = (T)1 / Ms;
-            const T Ai = p.A_cell ? p.A_cell[i] : p.A;
-            T sx = 0, sy = 0, sz = 0;
-            const long sxs = 1, sys = p.nx, szs = (long)p.nx * p.ny;
-#define MM_LINK(COND, OFF, ID2)                                            \
-            if (COND) {                                                    \
-                const long nb = i + (OFF);                                 \
-                const T w = link_weight<T>(p.A_cell, p.A, Ai, nb) * (ID2); \
-                sx += w * (m[nb] - mx);                                    \
-                sy += w * (m[N + nb] - my);                                \
-                sz += w * (m[2 * N + nb] - mz);                            \
+        T mx[VEC], my[VEC], mz[VEC];
+        LV::ld(m + i, mx); LV::ld(m + N + i, my); LV::ld(m + 2 * N + i, mz);
+        T Ms[VEC], A[VEC];
+        if (p.Ms_cell) LV::ld(p.Ms_cell + i, Ms); else { for (int v = 0; v < VEC; ++v) Ms[v] = p.Ms; }
+        if (p.A_cell) LV::ld(p.A_cell + i, A); else { for (int v = 0; v < VEC; ++v) A[v] = p.A; }
+        // exchange sums s = sum_links w_link / d^2 (m_nb - m_i), w_link the harmonic mean of A
+        T sx[VEC], sy_[VEC], sz_[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) { sx[v] = 0; sy_[v] = 0; sz_[v] = 0; }
+        // x links inside the vector and to the scalar neighbours at both ends
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int x = x0 + v;
+            if (x > 0) {
+                T nbx, nby, nbz, Anb;
+                if (v > 0) { nbx = mx[v - 1]; nby = my[v - 1]; nbz = mz[v - 1]; Anb = A[v - 1]; }
+                else { nbx = m[i - 1]; nby = m[N + i - 1]; nbz = m[2 * N + i - 1]; Anb = p.A_cell ? p.A_cell[i - 1] : p.A; }
+                const T w = (p.A_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
+                sx[v] += w * (nbx - mx[v]); sy_[v] += w * (nby - my[v]); sz_[v] += w * (nbz - mz[v]);
             }
-            MM_LINK(x > 0, -sxs, p.idx2)
-            MM_LINK(x < p.nx - 1, sxs, p.idx2)
-            MM_LINK(y > 0, -sys, p.idy2)
-            MM_LINK(y < p.ny - 1, sys, p.idy2)
-            MM_LINK(z > 0, -szs, p.idz2)
-            MM_LINK(z < p.nz - 1, szs, p.idz2)
-#undef MM_LINK
-            const T cex = (T)(2.0 / kMu0) * inv;
-            hex = cex * sx; hey = cex * sy; hez = cex * sz;
-            const T Ku = p.Ku_cell ? p.Ku_cell[i] : p.Ku;
-            if (Ku != (T)0) {
-                T ex = p.ex, ey = p.ey, ez = p.ez;
-                if (p.grain) {
-                    const int gi = p.grain[i];
-                    ex = p.axis_tab[3 * gi]; ey = p.axis_tab[3 * gi + 1]; ez = p.axis_tab[3 * gi + 2];
+            if (x < nx - 1) {
+                T nbx, nby, nbz, Anb;
+                if (v < VEC - 1) { nbx = mx[v + 1]; nby = my[v + 1]; nbz = mz[v + 1]; Anb = A[v + 1]; }
+                else { nbx = m[i + VEC]; nby = m[N + i + VEC]; nbz = m[2 * N + i + VEC]; Anb = p.A_cell ? p.A_cell[i + VEC] : p.A; }
+                const T w = (p.A_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
+                sx[v] += w * (nbx - mx[v]); sy_[v] += w * (nby - my[v]); sz_[v] += w * (nbz - mz[v]);
+            }
+        }
+        // y and z links: whole vectors of neighbours
+#define MM_VLINK(COND, OFF, ID2)                                                          \
+        if (COND) {                                                                       \
+            T nbx[VEC], nby[VEC], nbz[VEC], Anb[VEC];                                     \
+            LV::ld(m + i + (OFF), nbx); LV::ld(m + N + i + (OFF), nby); LV::ld(m + 2 * N + i + (OFF), nbz); \
+            if (p.A_cell) LV::ld(p.A_cell + i + (OFF), Anb);                              \
+            _Pragma("unroll") for (int v = 0; v < VEC; ++v) {                              \
+                const T w = (p.A_cell ? harmonic(A[v], Anb[v]) : p.A) * (ID2);            \
+                sx[v] += w * (nbx[v] - mx[v]); sy_[v] += w * (nby[v] - my[v]); sz_[v] += w * (nbz[v] - mz[v]); \
+            }                                                                             \
+        }
+        MM_VLINK(y > 0, -sy, p.idy2)
+        MM_VLINK(y < ny - 1, sy, p.idy2)
+        MM_VLINK(z > 0, -sz, p.idz2)
+        MM_VLINK(z < nz - 1, sz, p.idz2)
+#undef MM_VLINK
+        T Ku[VEC], al[VEC], zw[VEC], hdx[VEC], hdy[VEC], hdz[VEC];
+        if (p.Ku_cell) LV::ld(p.Ku_cell + i, Ku); else { for (int v = 0; v < VEC; ++v) Ku[v] = p.Ku; }
+        if (p.alpha_cell) LV::ld(p.alpha_cell + i, al); else { for (int v = 0; v < VEC; ++v) al[v] = p.alpha; }
+        if (p.zw) LV::ld(p.zw + i, zw); else { for (int v = 0; v < VEC; ++v) zw[v] = (T)1; }
+        if (p.hd) { LV::ld(p.hd + i, hdx); LV::ld(p.hd + N + i, hdy); LV::ld(p.hd + 2 * N + i, hdz); }
+        else { for (int v = 0; v < VEC; ++v) { hdx[v] = 0; hdy[v] = 0; hdz[v] = 0; } }
+        T kx[VEC], ky[VEC], kz[VEC];
+        T hxo[VEC], hyo[VEC], hzo[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            T hx = 0, hy = 0, hz = 0, hex = 0, hey = 0, hez = 0, hax = 0, hay = 0, haz = 0, hzx = 0, hzy = 0, hzz = 0;
+            T hdxv = 0, hdyv = 0, hdzv = 0;
+            if (Ms[v] != (T)0) {
+                const T inv = (T)1 / Ms[v];
+                const T cex = (T)(2.0 / kMu0) * inv;
+                hex = cex * sx[v]; hey = cex * sy_[v]; hez = cex * sz_[v];
+                if (Ku[v] != (T)0) {
+                    T ex = p.ex, ey = p.ey, ez = p.ez;
+                    if (p.grain) {
+                        const int gi = p.grain[i + v];
+                        ex = p.axis_tab[3 * gi]; ey = p.axis_tab[3 * gi + 1]; ez = p.axis_tab[3 * gi + 2];
+                    }
+                    const T c = (T)(2.0 / kMu0) * Ku[v] * inv * (ex * mx[v] + ey * my[v] + ez * mz[v]);
+                    hax = c * ex; hay = c * ey; haz = c * ez;
                 }
-                const T c = (T)(2.0 / kMu0) * Ku * inv * (ex * mx + ey * my + ez * mz);
-                hax = c * ex; hay = c * ey; haz = c * ez;
+                hzx = zw[v] * p.hx0; hzy = zw[v] * p.hy0; hzz = zw[v] * p.hz0;
+                hdxv = hdx[v]; hdyv = hdy[v]; hdzv = hdz[v];
+                hx = hdxv + hex + hax + hzx;
+                hy = hdyv + hey + hay + hzy;
+                hz = hdzv + hez + haz + hzz;
             }
-            const T w = p.zw ? p.zw[i] : (T)1;
-            hzx = w * p.hx0; hzy = w * p.hy0; hzz = w * p.hz0;
-            if (p.hd) { hdx = p.hd[i]; hdy = p.hd[N + i]; hdz = p.hd[2 * N + i]; }
-            hx = hdx + hex + hax + hzx;
-            hy = hdy + hey + hay + hzy;
-            hz = hdz + hez + haz + hzz;
+            hxo[v] = hx; hyo[v] = hy; hzo[v] = hz;
+            const T gp = (T)(-kGamma) / ((T)1 + al[v] * al[v]);
+            const T cx = my[v] * hz - mz[v] * hy, cy = mz[v] * hx - mx[v] * hz, cz = mx[v] * hy - my[v] * hx;
+            const T dx_ = my[v] * cz - mz[v] * cy, dy_ = mz[v] * cx - mx[v] * cz, dz_ = mx[v] * cy - my[v] * cx;
+            kx[v] = gp * (cx + al[v] * dx_); ky[v] = gp * (cy + al[v] * dy_); kz[v] = gp * (cz + al[v] * dz_);
+            if (!(isfinite(kx[v]) && isfinite(ky[v]) && isfinite(kz[v]))) red_nf = 1.0;
+            if (p.want_torque && Ms[v] != (T)0)
+                red_torque = fmax(red_torque, sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms[v]);
+            if (p.want_energy && Ms[v] != (T)0) {
+                const double f = -0.5 * kMu0 * p.V * (double)Ms[v];
+                red_e0 += f * ((double)mx[v] * hdxv + (double)my[v] * hdyv + (double)mz[v] * hdzv);
+                red_e1 += f * ((double)mx[v] * hex + (double)my[v] * hey + (double)mz[v] * hez);
+                red_e2 += f * ((double)mx[v] * hax + (double)my[v] * hay + (double)mz[v] * haz);
+                red_e3 += 2.0 * f * ((double)mx[v] * hzx + (double)my[v] * hzy + (double)mz[v] * hzz);
+            }
         }
-        if (p.h_out) { p.h_out[i] = hx; p.h_out[N + i] = hy; p.h_out[2 * N + i] = hz; }
-        const T al = p.alpha_cell ? p.alpha_cell[i] : p.alpha;
-        const T gp = (T)(-kGamma) / ((T)1 + al * al);
-        const T cx = my * hz - mz * hy, cy = mz * hx - mx * hz, cz = mx * hy - my * hx;
-        const T dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
-        const T kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
-        if (!(isfinite(kx) && isfinite(ky) && isfinite(kz))) red_nf = 1.0;
-        if (p.want_torque && Ms != (T)0)
-            red_torque = sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms;
-        if (p.want_energy && Ms != (T)0) {
-            const double f = -0.5 * kMu0 * p.V * (double)Ms;
-            red_e[0] = f * ((double)mx * hdx + (double)my * hdy + (double)mz * hdz);
-            red_e[1] = f * ((double)mx * hex + (double)my * hey + (double)mz * hez);
-            red_e[2] = f * ((double)mx * hax + (double)my * hay + (double)mz * haz);
-            red_e[3] = 2.0 * f * ((double)mx * hzx + (double)my * hzy + (double)mz * hzz);
-        }
-        if (p.k_out) { p.k_out[i] = kx; p.k_out[N + i] = ky; p.k_out[2 * N + i] = kz; }
+        if (p.h_out) { LV::st(p.h_out + i, hxo); LV::st(p.h_out + N + i, hyo); LV::st(p.h_out + 2 * N + i, hzo); }
+        if (p.k_out) { LV::st(p.k_out + i, kx); LV::st(p.k_out + N + i, ky); LV::st(p.k_out + 2 * N + i, kz); }
         if (p.acc_out) {
-            T ax = (T)p.acc_b * kx, ay = (T)p.acc_b * ky, az = (T)p.acc_b * kz;
-            if (p.acc_in) { ax += p.acc_in[i]; ay += p.acc_in[N + i]; az += p.acc_in[2 * N + i]; }
-            p.acc_out[i] = ax; p.acc_out[N + i] = ay; p.acc_out[2 * N + i] = az;
+            T ax[VEC], ay[VEC], az[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) { ax[v] = p.acc_bT * kx[v]; ay[v] = p.acc_bT * ky[v]; az[v] = p.acc_bT * kz[v]; }
+            if (p.acc_in) {
+                T bx[VEC], by[VEC], bz[VEC];
+                LV::ld(p.acc_in + i, bx); LV::ld(p.acc_in + N + i, by); LV::ld(p.acc_in + 2 * N + i, bz);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) { ax[v] += bx[v]; ay[v] += by[v]; az[v] += bz[v]; }
+            }
+            LV::st(p.acc_out + i, ax); LV::st(p.acc_out + N + i, ay); LV::st(p.acc_out + 2 * N + i, az);
         }
         if (p.next || p.want_err) {
-            T sxn = (T)p.ck * kx, syn = (T)p.ck * ky, szn = (T)p.ck * kz;
-            double ex_ = p.eb_k * kx, ey_ = p.eb_k * ky, ez_ = p.eb_k * kz;
+            T snx[VEC], sny[VEC], snz[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) { snx[v] = p.ckT * kx[v]; sny[v] = p.ckT * ky[v]; snz[v] = p.ckT * kz[v]; }
+            double ex_[VEC], ey_[VEC], ez_[VEC];
+            if (p.want_err) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) { ex_[v] = p.eb_k * kx[v]; ey_[v] = p.eb_k * ky[v]; ez_[v] = p.eb_k * kz[v]; }
+            }
             for (int q = 0; q < p.nk; ++q) {
                 const T* kq = p.kin[q];
-                const T ax = kq[i], ay = kq[N + i], az = kq[2 * N + i];
-                sxn += (T)p.kc[q] * ax; syn += (T)p.kc[q] * ay; szn += (T)p.kc[q] * az;
-                if (p.want_err) { ex_ += p.eb[q] * ax; ey_ += p.eb[q] * ay; ez_ += p.eb[q] * az; }
+                T ax[VEC], ay[VEC], az[VEC];
+                LV::ld(kq + i, ax); LV::ld(kq + N + i, ay); LV::ld(kq + 2 * N + i, az);
+                const T c = p.kcT[q];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) { snx[v] += c * ax[v]; sny[v] += c * ay[v]; snz[v] += c * az[v]; }
+                if (p.want_err) {
+                    const double e = p.eb[q];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) { ex_[v] += e * ax[v]; ey_[v] += e * ay[v]; ez_[v] += e * az[v]; }
+                }
             }
-            const T m0x = p.mn[i], m0y = p.mn[N + i], m0z = p.mn[2 * N + i];
+            T m0x[VEC], m0y[VEC], m0z[VEC];
+            LV::ld(p.mn + i, m0x); LV::ld(p.mn + N + i, m0y); LV::ld(p.mn + 2 * N + i, m0z);
             if (p.want_err) {
-                const double sc_x = p.atol + p.rtol * fmax(fabs((double)m0x), fabs((double)mx));
-                const double sc_y = p.atol + p.rtol * fmax(fabs((double)m0y), fabs((double)my));
-                const double sc_z = p.atol + p.rtol * fmax(fabs((double)m0z), fabs((double)mz));
-                red_err = fmax(fmax(fabs(p.dt * ex_) / sc_x, fabs(p.dt * ey_) / sc_y), fabs(p.dt * ez_) / sc_z);
-                if (!isfinite(red_err)) red_nf = 1.0;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const double scx = p.atol + p.rtol * fmax(fabs((double)m0x[v]), fabs((double)mx[v]));
+                    const double scy = p.atol + p.rtol * fmax(fabs((double)m0y[v]), fabs((double)my[v]));
+                    const double scz = p.atol + p.rtol * fmax(fabs((double)m0z[v]), fabs((double)mz[v]));
+                    const double r = fmax(fmax(fabs(p.dt * ex_[v]) / scx, fabs(p.dt * ey_[v]) / scy),
+                                          fabs(p.dt * ez_[v]) / scz);
+                    if (!isfinite(r)) red_nf = 1.0;
+                    red_err = fmax(red_err, r);
+                }
             }
             if (p.next) {
-                const T dt = (T)p.dt;
-                T nx_ = m0x + dt * sxn, ny_ = m0y + dt * syn, nz_ = m0z + dt * szn;
-                if (p.renorm) {
-                    const T n2 = nx_ * nx_ + ny_ * ny_ + nz_ * nz_;
-                    if (n2 > (T)0) {
-                        const T s = (T)1 / sqrt(n2);
-                        nx_ *= s; ny_ *= s; nz_ *= s;
+                const T dt = p.dtT;
+                T ox[VEC], oy[VEC], oz[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    T a = m0x[v] + dt * snx[v], b = m0y[v] + dt * sny[v], c = m0z[v] + dt * snz[v];
+                    if (p.renorm) {
+                        const T n2 = a * a + b * b + c * c;
+                        if (n2 > (T)0) {
+                            const T s = (T)1 / sqrt(n2);
+                            a *= s; b *= s; c *= s;
+                        }
                     }
+                    ox[v] = a; oy[v] = b; oz[v] = c;
                 }
-                p.next[i] = nx_; p.next[N + i] = ny_; p.next[2 * N + i] = nz_;
+                LV::st(p.next + i, ox); LV::st(p.next + N + i, oy); LV::st(p.next + 2 * N + i, oz);
             }
         }
     }
     // ---- block reduction (all threads participate) ----
     if (p.partials) {
         __shared__ double red[kStageThreads / 32][kNPart];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        double vals[kNPart] = {red_torque, red_e[0], red_e[1], red_e[2], red_e[3], red_err, red_nf, 0.0};
+        const int tid = threadIdx.y * kBX + threadIdx.x;
+        const int lane = tid & 31, wid = tid >> 5;
+        double vals[kNPart] = {red_torque, red_e0, red_e1, red_e2, red_e3, red_err, red_nf, 0.0};
         vals[R_TORQUE] = warp_max(vals[R_TORQUE]);
         vals[R_ERR] = warp_max(vals[R_ERR]);
         vals[R_NONFINITE] = warp_max(vals[R_NONFINITE]);
@@ -164,14 +258,15 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
             for (int q = 0; q < kNPart; ++q) red[wid][q] = vals[q];
         }
         __syncthreads();
-        if (threadIdx.x < kNPart) {
-            const int q = threadIdx.x;
+        if (tid < kNPart) {
+            const int q = tid;
             double acc = red[0][q];
             for (int w = 1; w < kStageThreads / 32; ++w) {
                 const double v = red[w][q];
                 acc = (q == R_TORQUE || q == R_ERR || q == R_NONFINITE) ? fmax(acc, v) : acc + v;
             }
-            p.partials[(long)blockIdx.x * kNPart + q] = acc;
+            const long b = ((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            p.partials[b * kNPart + q] = acc;
         }
     }
 }
@@ -246,10 +341,43 @@ template <typename T> void launch_combine(const T* mn, const T* const* kin, cons
     combine_kernel<T><<<(unsigned)((3 * N + 255) / 256), 256, 0, st>>>(p);
 }
 
-template <typename T> void launch_stage(const StageParams<T>& p, cudaStream_t st, int* nblocks) {
-    const int nb = (int)((p.N + kStageThreads - 1) / kStageThreads);
-    *nblocks = nb;
-    stage_kernel<T><<<nb, kStageThreads, 0, st>>>(p);
+template <typename T> int stage_vec(int nx);
+template <> int stage_vec<float>(int nx) { return nx % 4 == 0 ? 4 : 1; }
+template <> int stage_vec<double>(int nx) { return nx % 2 == 0 ? 2 : 1; }
+
+// an upper bound on the blocks launch_stage uses (the scalar path has the most)
+template <typename T> int stage_blocks(int nx, int ny, int nz) {
+    const int gx = (nx + kBX - 1) / kBX;
+    const int gy = (ny + kBY - 1) / kBY;
+    return gx * gy * nz;
+}
+
+static bool al16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+// the vector path needs every per-cell array 16-byte aligned (caller buffers may be views)
+template <typename T> static bool all_aligned(const StageParams<T>& p) {
+    const void* ptrs[] = {p.m, p.hd, p.Ms_cell, p.A_cell, p.Ku_cell, p.alpha_cell, p.zw, p.h_out, p.k_out,
+                          p.mn, p.next, p.acc_in, p.acc_out};
+    for (const void* q : ptrs)
+        if (!al16(q)) return false;
+    for (int q = 0; q < p.nk; ++q)
+        if (!al16(p.kin[q])) return false;
+    return true;
+}
+
+template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t st, int* nblocks) {
+    StageParams<T> p = p0;
+    for (int q = 0; q < 7; ++q) p.kcT[q] = (T)p.kc[q];
+    p.ckT = (T)p.ck;
+    p.dtT = (T)p.dt;
+    p.acc_bT = (T)p.acc_b;
+    const int vec = all_aligned(p) ? stage_vec<T>(p.nx) : 1;
+    dim3 block(kBX, kBY);
+    dim3 grid((p.nx / vec + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, p.nz);
+    *nblocks = (int)(grid.x * grid.y * grid.z);
+    if (vec == 1) stage_kernel<T, 1><<<grid, block, 0, st>>>(p);
+    else if constexpr (sizeof(T) == 4) stage_kernel<T, 4><<<grid, block, 0, st>>>(p);
+    else stage_kernel<T, 2><<<grid, block, 0, st>>>(p);
 }
 
 void launch_finalize(const double* partials, int nblocks, double* scalars, cudaStream_t st) {
@@ -265,6 +393,8 @@ template <typename T> void launch_renorm_copy(const T* src, T* dst, long N, cuda
     renorm_copy_kernel<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(src, dst, N);
 }
 
+template int stage_blocks<float>(int, int, int);
+template int stage_blocks<double>(int, int, int);
 template void launch_stage<float>(const StageParams<float>&, cudaStream_t, int*);
 template void launch_stage<double>(const StageParams<double>&, cudaStream_t, int*);
 template void launch_convert<float>(const double*, float*, long, cudaStream_t);

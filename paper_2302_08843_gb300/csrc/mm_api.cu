@@ -279,7 +279,7 @@ template <typename T> mm_status run_demag(mm_state* s, const void* m) {
 }
 
 template <typename T> mm_status run_stage(mm_state* s, StageParams<T>& p, bool reduce) {
-    const int nb = (int)((s->N + 255) / 256);
+    const int nb = stage_blocks<T>(s->g.nx, s->g.ny, s->g.nz);
     if (reduce) {
         MM_TRY(ensure_partials(s, nb));
         p.partials = s->partials;
