@@ -110,4 +110,63 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8_half(C* a) {
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
+// cos and sin of pi k / 8, k = 0..15
+__host__ __device__ constexpr double c16(int k) {
+    return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
+         : k == 3 ? 0.38268343236508977173 : k == 4 ? 0.0 : k == 5 ? -0.38268343236508977173
+         : k == 6 ? -0.70710678118654752440 : k == 7 ? -0.92387953251128675613 : k == 8 ? -1.0
+         : k == 9 ? -0.92387953251128675613 : k == 10 ? -0.70710678118654752440
+         : k == 11 ? -0.38268343236508977173 : k == 12 ? 0.0 : k == 13 ? 0.38268343236508977173
+         : k == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
+}
+__host__ __device__ constexpr double s16(int k) { return c16((k + 12) & 15); }   // sin(x) = cos(x - pi/2)
+
+// a * exp(DIR 2 pi i K / 16)
+template <int DIR, int K, typename C> __device__ __forceinline__ C mul_w16(C a) {
+    using T = decltype(C::x);
+    constexpr int k = K & 15;
+    if constexpr (k == 0) {
+        return a;
+    } else if constexpr (k == 4) {
+        return mul_i<DIR>(a);
+    } else if constexpr (k == 8) {
+        return mk<C>(-a.x, -a.y);
+    } else if constexpr (k == 12) {
+        return mul_i<-DIR>(a);
+    } else {
+        constexpr T c = (T)c16(k), sn = (T)(DIR * s16(k));
+        return mk<C>(a.x * c - a.y * sn, a.x * sn + a.y * c);
+    }
+}
+
+// DFT16 in place (radix 4 x 4); HALF: inputs 8..15 are known zeros
+template <int DIR, bool HALF, typename C> __device__ __forceinline__ void dft16(C* a) {
+    C y0[4], y1[4], y2[4], y3[4];
+    C* y[4] = {y0, y1, y2, y3};
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C b0 = a[n2], b1 = a[4 + n2];
+        if (HALF) {
+            y[n2][0] = cadd(b0, b1);
+            y[n2][2] = csub(b0, b1);
+            y[n2][1] = cadd(b0, mul_i<DIR>(b1));
+            y[n2][3] = csub(b0, mul_i<DIR>(b1));
+        } else {
+            C b2 = a[8 + n2], b3 = a[12 + n2];
+            dft4<DIR>(b0, b1, b2, b3);
+            y[n2][0] = b0; y[n2][1] = b1; y[n2][2] = b2; y[n2][3] = b3;
+        }
+    }
+    // twiddles W16^(n2 k1)
+    y1[1] = mul_w16<DIR, 1>(y1[1]); y1[2] = mul_w16<DIR, 2>(y1[2]); y1[3] = mul_w16<DIR, 3>(y1[3]);
+    y2[1] = mul_w16<DIR, 2>(y2[1]); y2[2] = mul_w16<DIR, 4>(y2[2]); y2[3] = mul_w16<DIR, 6>(y2[3]);
+    y3[1] = mul_w16<DIR, 3>(y3[1]); y3[2] = mul_w16<DIR, 6>(y3[2]); y3[3] = mul_w16<DIR, 9>(y3[3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C b0 = y0[k1], b1 = y1[k1], b2 = y2[k1], b3 = y3[k1];
+        dft4<DIR>(b0, b1, b2, b3);
+        a[k1] = b0; a[k1 + 4] = b1; a[k1 + 8] = b2; a[k1 + 12] = b3;
+    }
+}
+
 }  // namespace mm

@@ -16,6 +16,7 @@ struct DemagDims {
     int LX, LY, LZ;      // padded FFT extents
     int KX;              // LX/2 + 1 spectrum columns
     int KXS;             // row stride of S1/S2 and of the tensor spectrum (elements)
+    int* err = nullptr;  // device error word for bounded-wait failures; null: no TMA kernels
 };
 
 // CUDA-event timing of kernel launches on a stream (inactive unless enabled).
@@ -77,6 +78,7 @@ struct StageParams {
     double* partials;            // [number of blocks][kNPart]
     // the coefficients above in the field type (filled by launch_stage)
     T kcT[7], ckT, dtT, acc_bT;
+    T cex_u, cani_u, gp_u;       // 2/(mu0 Ms), 2 Ku/(mu0 Ms), -gamma/(1+alpha^2) for uniform material
 };
 
 template <typename T> void launch_stage(const StageParams<T>& p, cudaStream_t st, int* nblocks);

@@ -18,10 +18,14 @@
 // through shared memory with a padded stride.  The all-zero padded half of
 // every forward transform is never loaded nor transformed (FftLine ZIN) and
 // only the kept half of every inverse output is stored.
+#include <cudaTypedefs.h>
+
 #include <cstdio>
+#include <mutex>
 
 #include "demag.h"
 #include "fft_engine.cuh"
+#include "tma.cuh"
 
 namespace mm {
 
@@ -33,11 +37,11 @@ cudaError_t upload_twiddles(const double2* w64, const float2* w32) {
 
 // ------------------------------------------------------------------ P1 ----
 template <typename T, int LX, int NL>
-__global__ void __launch_bounds__(NL * FftLine<T, LX, -1, (LX > 1)>::TPL)
+__global__ void __launch_bounds__(NL * Fft<T, LX, -1, (LX > 1)>::TPL)
 p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell, T Ms_const,
              typename Cplx<T>::type* __restrict__ S1) {
     using C = typename Cplx<T>::type;
-    using F = FftLine<T, LX, -1, (LX > 1)>;
+    using F = Fft<T, LX, -1, (LX > 1)>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     constexpr int LS = NL + 1;
@@ -69,7 +73,7 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
     C v[F::NR];
 #pragma unroll
     for (int r = 0; r < F::NR; ++r) {
-        if (LX == 1 || r < F::NR / 2) v[r] = s[(j + r * F::TPL) * LS + line];
+        if (F::in_live(r)) v[r] = s[F::in_index(j, r) * LS + line];
         else v[r] = mk<C>(0, 0);
     }
     F::run(v, s + line, LS, j);
@@ -93,12 +97,12 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
 // DIR = -1: S1 (ny rows) -> S2 (Py rows), forward, zero upper half.
 // DIR = +1: S2 (Py rows) -> S1 (ny rows), inverse, keep the lower half.
 template <typename T, int LY, int B, int G, int DIR>
-__global__ void __launch_bounds__(B * G * FftLine<T, LY, DIR, (DIR < 0 && LY > 1)>::TPL)
+__global__ void __launch_bounds__(B * G * Fft<T, LY, DIR, (DIR < 0 && LY > 1)>::TPL)
 p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
          typename Cplx<T>::type* __restrict__ out) {
     using C = typename Cplx<T>::type;
     constexpr bool ZIN = DIR < 0 && LY > 1;
-    using F = FftLine<T, LY, DIR, ZIN>;
+    using F = Fft<T, LY, DIR, ZIN>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     constexpr int NL = B * G;
@@ -115,9 +119,9 @@ p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
     C v[F::NR];
 #pragma unroll
     for (int r = 0; r < F::NR; ++r) {
-        const int e = j + r * F::TPL;
+        const int e = F::in_index(j, r);
         v[r] = mk<C>(0, 0);
-        if (valid && (!ZIN || r < F::NR / 2) && e < rows_in) v[r] = src[(long)e * d.KXS];
+        if (valid && F::in_live(r) && e < rows_in) v[r] = src[(long)e * d.KXS];
     }
     F::run(v, s + line, NL, j);
     if (valid) {
@@ -125,6 +129,88 @@ p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
         for (int r = 0; r < F::NR; ++r) {
             const int e = j + r * F::TPL;
             if (e < rows_out) dst[(long)e * d.KXS] = v[r];
+        }
+    }
+}
+
+// ------------------------------------------------------- P2 / P4 (TMA) ----
+// Persistent, double-buffered variant for FP32: each CTA walks tiles of B kx
+// columns x all rows of one (component, z) plane; the tile after next is
+// fetched by the tensor-memory accelerator into the shared-memory slot the
+// finished tile frees, so HBM traffic overlaps the transforms.  The engine uses
+// the tile's slot as its exchange scratch.  Every mbarrier wait is bounded;
+// on timeout the CTA records kErrTmaTimeout, waits (bounded) for its other
+// copy in flight and leaves.
+template <typename T, int L, int B, int DIR>
+__global__ void __launch_bounds__(B * Fft<T, L, DIR, (DIR < 0 && L > 1)>::TPL, 1)
+p_y_tma(DemagDims d, const __grid_constant__ CUtensorMap in_map, typename Cplx<T>::type* __restrict__ out,
+        int box_rows, int nboxes) {
+    using C = typename Cplx<T>::type;
+    constexpr bool ZIN = DIR < 0 && L > 1;
+    using F = Fft<T, L, DIR, ZIN>;
+    constexpr int TPL = F::TPL, NR = F::NR;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    C* slot0 = reinterpret_cast<C*>(smtma);
+    C* slot1 = slot0 + L * B;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)L * B * sizeof(C));
+    const int tid = threadIdx.x;
+    const int line = tid % B, j = tid / B;
+    const int rows_in = DIR < 0 ? d.ny : L;
+    const int rows_out = DIR < 0 ? L : d.ny;
+    const int nkt = (d.KX + B - 1) / B;
+    const int ntiles = nkt * 3 * d.nz;
+    const uint32_t tile_bytes = (uint32_t)(nboxes * box_rows * B * sizeof(C));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int sl) {
+        const int kt = t % nkt, cz = t / nkt;
+        C* dst = sl ? slot1 : slot0;
+        mbar_arrive_expect_tx(&bar[sl], tile_bytes);
+        for (int b = 0; b < nboxes; ++b)
+            tma_load_3d(dst + (size_t)b * box_rows * B, &in_map, &bar[sl], kt * B, b * box_rows, cz);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    }
+    int i = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
+        const int sl = i & 1;
+        C* cur = sl ? slot1 : slot0;
+        const bool ok = mbar_wait_bounded(&bar[sl], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((i + 1) >> 1) & 1);
+            }
+            return;
+        }
+        C v[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int e = F::in_index(j, r);
+            v[r] = (F::in_live(r) && e < rows_in) ? cur[e * B + line] : mk<C>(0, 0);
+        }
+        F::run(v, cur + line, B, j);
+        const int kt = t % nkt, cz = t / nkt;
+        const int kx = kt * B + line;
+        if (kx < d.KX) {
+            C* dst = out + ((long)cz * rows_out) * d.KXS + kx;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int e = j + r * TPL;
+                if (e < rows_out) dst[(long)e * d.KXS] = v[r];
+            }
+        }
+        __syncthreads();   // every thread is done with this slot
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * gridDim.x, sl);
         }
     }
 }
@@ -142,12 +228,12 @@ template <typename T> constexpr int p3_min_blocks(int threads) {
 // half straight to global memory.  Only one component's registers are live at
 // a time, which keeps the kernel at four CTAs per SM.
 template <typename T, int LZ, int B, int G>
-__global__ void __launch_bounds__(B * G * FftLine<T, LZ, -1, (LZ > 1)>::TPL,
-                                  p3_min_blocks<T>(B * G * FftLine<T, LZ, -1, (LZ > 1)>::TPL))
+__global__ void __launch_bounds__(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL,
+                                  p3_min_blocks<T>(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL))
 p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restrict__ tens) {
     using C = typename Cplx<T>::type;
-    using FF = FftLine<T, LZ, -1, (LZ > 1)>;
-    using FI = FftLine<T, LZ, +1, false>;
+    using FF = Fft<T, LZ, -1, (LZ > 1)>;
+    using FI = Fft<T, LZ, +1, false>;
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int NL = B * G;
     constexpr int NR = FF::NR, TPL = FF::TPL;
@@ -170,25 +256,26 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
     C* col = S2 + (long)ky * d.KXS + kx;            // element (c, z) at col[c*cstride + z*LY*KXS]
     const long zs = (long)LY * d.KXS;
 
-    {   // all loads in flight together, parked at this thread's own positions
-        C in[3][NIN];
+    {   // all loads in flight together, parked at this thread's own (pattern) positions
+        C in[3][NR];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int r = 0; r < NIN; ++r) {
-                const int z = j + r * TPL;
-                in[c][r] = (valid && z < d.nz) ? col[c * cstride + z * zs] : mk<C>(0, 0);
+            for (int r = 0; r < NR; ++r) {
+                const int z = FF::in_index(j, r);
+                in[c][r] = (FF::in_live(r) && valid && z < d.nz) ? col[c * cstride + z * zs] : mk<C>(0, 0);
             }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int r = 0; r < NIN; ++r) area[c][(j + r * TPL) * NL + line] = in[c][r];
+            for (int r = 0; r < NR; ++r)
+                if (FF::in_live(r)) area[c][(j + r * TPL) * NL + line] = in[c][r];
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         C v[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = r < NIN ? area[c][(j + r * TPL) * NL + line] : mk<C>(0, 0);
+        for (int r = 0; r < NR; ++r) v[r] = FF::in_live(r) ? area[c][(j + r * TPL) * NL + line] : mk<C>(0, 0);
         FF::run(v, area[c] + line, NL, j);
 #pragma unroll
         for (int r = 0; r < NR; ++r) area[c][(j + r * TPL) * NL + line] = v[r];
@@ -234,12 +321,215 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
     }
 }
 
+// Register-resident variant (FP32): each thread keeps its 16 values of all
+// three components from the first load to the last store; shared memory only
+// carries the exchanges inside each transform (one per 128-point transform).
+template <typename T, int LZ, int B, int G>
+__global__ void __launch_bounds__(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL,
+                                  (384 / (B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL)) > 1
+                                      ? 384 / (B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL) : 1)
+p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restrict__ tens) {
+    using C = typename Cplx<T>::type;
+    using FF = Fft<T, LZ, -1, (LZ > 1)>;
+    using FI = Fft<T, LZ, +1, false>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    constexpr int NL = B * G;
+    constexpr int NR = FF::NR, TPL = FF::TPL;
+    constexpr int NOUT = LZ == 1 ? 1 : NR / 2;
+    const int tid = threadIdx.x;
+    const int line = tid % NL, j = tid / NL;
+    const int kl = line % B, g = line / B;
+    const int kx = blockIdx.x * B + kl;
+    const int kyi = blockIdx.y * G + g;           // (folded ky, side) pairs, side fastest
+    const int p = kyi >> 1, side = kyi & 1;
+    const int LY = d.LY;
+    const int KY2 = LY / 2 + 1;
+    const bool valid = kx < d.KX && p < KY2 && (side == 0 || (p > 0 && 2 * p < LY));
+    const int ky = side ? LY - p : p;
+    const long cstride = (long)d.nz * LY * d.KXS;
+    C* col = S2 + (long)ky * d.KXS + kx;
+    const long zs = (long)LY * d.KXS;
+
+    C vx[NR], vy[NR], vz[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int z = FF::in_index(j, r);
+        vx[r] = vy[r] = vz[r] = mk<C>(0, 0);
+        if (valid && FF::in_live(r) && z < d.nz) {
+            vx[r] = col[z * zs];
+            vy[r] = col[cstride + z * zs];
+            vz[r] = col[2 * cstride + z * zs];
+        }
+    }
+    FF::run(vx, s + line, NL, j);
+    FF::run(vy, s + line, NL, j);
+    FF::run(vz, s + line, NL, j);
+    const int KZ2 = LZ / 2 + 1;
+    const long tcomp = (long)KZ2 * KY2 * d.KXS;
+    const T sy = side ? (T)-1 : (T)1;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int kz = j + r * TPL;
+        const int kzf = (2 * kz <= LZ) ? kz : LZ - kz;
+        const T sz = (2 * kz <= LZ) ? (T)1 : (T)-1;
+        T txx = 0, txy = 0, txz = 0, tyy = 0, tyz = 0, tzz = 0;
+        if (valid) {
+            const T* tp = tens + ((long)kzf * KY2 + p) * d.KXS + kx;
+            txx = __ldg(tp);
+            txy = sy * __ldg(tp + tcomp);
+            txz = sz * __ldg(tp + 2 * tcomp);
+            tyy = __ldg(tp + 3 * tcomp);
+            tyz = sy * sz * __ldg(tp + 4 * tcomp);
+            tzz = __ldg(tp + 5 * tcomp);
+        }
+        const C mx = vx[r], my = vy[r], mz = vz[r];
+        vx[r] = mk<C>(txx * mx.x + txy * my.x + txz * mz.x, txx * mx.y + txy * my.y + txz * mz.y);
+        vy[r] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
+        vz[r] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
+    }
+    FI::run(vx, s + line, NL, j);
+    FI::run(vy, s + line, NL, j);
+    FI::run(vz, s + line, NL, j);
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) {
+            const int z = j + r * TPL;
+            if (z < d.nz) {
+                col[z * zs] = vx[r];
+                col[cstride + z * zs] = vy[r];
+                col[2 * cstride + z * zs] = vz[r];
+            }
+        }
+    }
+}
+
+// Persistent TMA variant of the register-resident z pass (FP32, Pz <= 256):
+// tile = (16 kx columns, one ky); tiles run ky = 0, 1, Py-1, 2, Py-2, ... so
+// that the two wave numbers sharing a tensor slice are neighbours in time.
+// Each slot holds the tile's three z-columns (TMA box 16 x 1 x nz x 3 of S2)
+// and its tensor slice (box 16 x 1 x (Pz/2+1) x 6); the S2 part doubles as
+// the transforms' exchange scratch once the registers are loaded.
+template <int LZ, int B>
+__global__ void __launch_bounds__(B * Fft<float, LZ, -1, (LZ > 1)>::TPL, 2)
+p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_constant__ CUtensorMap t_map,
+         float2* __restrict__ S2, int slot_bytes, int s2_bytes) {
+    using C = float2;
+    using FF = Fft<float, LZ, -1, (LZ > 1)>;
+    using FI = Fft<float, LZ, +1, false>;
+    constexpr int NR = FF::NR, TPL = FF::TPL;
+    constexpr int NOUT = LZ == 1 ? 1 : NR / 2;
+    constexpr int KZ2 = LZ / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes);
+    const int tid = threadIdx.x;
+    const int line = tid % B, j = tid / B;
+    const int nz = d.nz, LY = d.LY;
+    const int nkt = (d.KX + B - 1) / B;
+    const int ntiles = nkt * LY;
+    const uint32_t tx_bytes = (uint32_t)(3 * nz * B * sizeof(C) + 6 * KZ2 * B * sizeof(float));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto ky_of = [&](int kyo, int& p, int& side) {
+        p = (kyo + 1) >> 1;
+        side = (kyo > 0 && (kyo & 1) == 0) ? 1 : 0;
+        return side ? LY - p : p;
+    };
+    auto issue = [&](int t, int sl) {
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        const int ky = ky_of(kyo, p, side);
+        unsigned char* base = smtma + (size_t)sl * slot_bytes;
+        mbar_arrive_expect_tx(&bar[sl], tx_bytes);
+        tma_load_4d(base, &s2_map, &bar[sl], kt * B, ky, 0, 0);
+        tma_load_4d(base + s2_bytes, &t_map, &bar[sl], kt * B, p, 0, 0);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    }
+    int i = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
+        const int sl = i & 1;
+        unsigned char* base = smtma + (size_t)sl * slot_bytes;
+        C* cs = reinterpret_cast<C*>(base);                       // [c][z][kx]
+        const float* ts = reinterpret_cast<const float*>(base + s2_bytes);   // [comp][kz'][kx]
+        const bool ok = mbar_wait_bounded(&bar[sl], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((i + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        const int ky = ky_of(kyo, p, side);
+        C vx[NR], vy[NR], vz[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int z = FF::in_index(j, r);
+            const bool live = FF::in_live(r) && z < nz;
+            vx[r] = live ? cs[(0 * nz + z) * B + line] : mk<C>(0, 0);
+            vy[r] = live ? cs[(1 * nz + z) * B + line] : mk<C>(0, 0);
+            vz[r] = live ? cs[(2 * nz + z) * B + line] : mk<C>(0, 0);
+        }
+        FF::run(vx, cs + line, B, j);
+        FF::run(vy, cs + line, B, j);
+        FF::run(vz, cs + line, B, j);
+        const float sy = side ? -1.f : 1.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int kz = j + r * TPL;
+            const int kzf = (2 * kz <= LZ) ? kz : LZ - kz;
+            const float sz = (2 * kz <= LZ) ? 1.f : -1.f;
+            const float txx = ts[(0 * KZ2 + kzf) * B + line];
+            const float txy = sy * ts[(1 * KZ2 + kzf) * B + line];
+            const float txz = sz * ts[(2 * KZ2 + kzf) * B + line];
+            const float tyy = ts[(3 * KZ2 + kzf) * B + line];
+            const float tyz = sy * sz * ts[(4 * KZ2 + kzf) * B + line];
+            const float tzz = ts[(5 * KZ2 + kzf) * B + line];
+            const C mx = vx[r], my = vy[r], mz = vz[r];
+            vx[r] = mk<C>(txx * mx.x + txy * my.x + txz * mz.x, txx * mx.y + txy * my.y + txz * mz.y);
+            vy[r] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
+            vz[r] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
+        }
+        FI::run(vx, cs + line, B, j);
+        FI::run(vy, cs + line, B, j);
+        FI::run(vz, cs + line, B, j);
+        const int kx = kt * B + line;
+        if (kx < d.KX) {
+            const long cstride = (long)nz * LY * d.KXS, zs = (long)LY * d.KXS;
+            C* col = S2 + (long)ky * d.KXS + kx;
+#pragma unroll
+            for (int r = 0; r < NOUT; ++r) {
+                const int z = j + r * TPL;
+                if (z < nz) {
+                    col[z * zs] = vx[r];
+                    col[cstride + z * zs] = vy[r];
+                    col[2 * cstride + z * zs] = vz[r];
+                }
+            }
+        }
+        __syncthreads();   // every thread is done with this slot
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * gridDim.x, sl);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ P5 ----
 template <typename T, int LX, int NL>
-__global__ void __launch_bounds__(NL * FftLine<T, LX, +1, false>::TPL)
+__global__ void __launch_bounds__(NL * Fft<T, LX, +1, false>::TPL)
 p5_x_inverse(DemagDims d, const typename Cplx<T>::type* __restrict__ S1, T* __restrict__ h) {
     using C = typename Cplx<T>::type;
-    using F = FftLine<T, LX, +1, false>;
+    using F = Fft<T, LX, +1, false>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
     constexpr int LS = NL + 1;
@@ -283,15 +573,18 @@ template <typename T> struct Geo;
 template <> struct Geo<float> { static constexpr int BS = 16; };   // 16 x 8 B = 128 B rows
 template <> struct Geo<double> { static constexpr int BS = 8; };   // 8 x 16 B = 128 B rows
 
-template <int L> constexpr int tpl_of() { return L >= 8 ? L / 8 : 1; }
+// threads per line of the engine a pass uses (forward and inverse engines of
+// one precision and length have the same thread count)
+template <typename T, int L> constexpr int tpl_of() { return Fft<T, L, +1, false>::TPL; }
 // lines per CTA for the x passes: about 256 threads
-template <int L> constexpr int nl_x() { return tpl_of<L>() >= 256 ? 1 : 256 / tpl_of<L>(); }
+template <typename T, int L> constexpr int nl_x() { return tpl_of<T, L>() >= 256 ? 1 : 256 / tpl_of<T, L>(); }
 // kx columns per CTA for strided passes: 128-byte rows, at most 512 threads per group
 template <typename T, int L> constexpr int b_of() {
-    return (Geo<T>::BS * tpl_of<L>() <= 512) ? Geo<T>::BS : ((512 / tpl_of<L>()) < 2 ? 2 : 512 / tpl_of<L>());
+    return (Geo<T>::BS * tpl_of<T, L>() <= 512) ? Geo<T>::BS
+                                                : ((512 / tpl_of<T, L>()) < 2 ? 2 : 512 / tpl_of<T, L>());
 }
 template <typename T, int L> constexpr int g_of() {
-    return (b_of<T, L>() * tpl_of<L>() >= 256) ? 1 : 256 / (b_of<T, L>() * tpl_of<L>());
+    return (b_of<T, L>() * tpl_of<T, L>() >= 256) ? 1 : 256 / (b_of<T, L>() * tpl_of<T, L>());
 }
 
 template <typename K> static void set_smem(K kernel, size_t bytes) {
@@ -300,26 +593,26 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 
 template <typename T, int L> static void launch_p1(const DemagDims& d, const T* m, const T* Ms_cell, T Ms,
                                                    typename Cplx<T>::type* S1, cudaStream_t st) {
-    constexpr int NL = nl_x<L>();
+    constexpr int NL = nl_x<T, L>();
     using C = typename Cplx<T>::type;
     const size_t sm = (size_t)L * (NL + 1) * sizeof(C);
     const long rows = 3L * d.ny * d.nz;
     const unsigned grid = (unsigned)((rows + 2 * NL - 1) / (2 * NL));
     auto k = p1_x_forward<T, L, NL>;
     set_smem(k, sm);
-    k<<<grid, NL * tpl_of<L>(), sm, st>>>(d, m, Ms_cell, Ms, S1);
+    k<<<grid, NL * tpl_of<T, L>(), sm, st>>>(d, m, Ms_cell, Ms, S1);
 }
 
 template <typename T, int L> static void launch_p5(const DemagDims& d, const typename Cplx<T>::type* S1, T* h,
                                                    cudaStream_t st) {
-    constexpr int NL = nl_x<L>();
+    constexpr int NL = nl_x<T, L>();
     using C = typename Cplx<T>::type;
     const size_t sm = (size_t)L * (NL + 1) * sizeof(C);
     const long rows = 3L * d.ny * d.nz;
     const unsigned grid = (unsigned)((rows + 2 * NL - 1) / (2 * NL));
     auto k = p5_x_inverse<T, L, NL>;
     set_smem(k, sm);
-    k<<<grid, NL * tpl_of<L>(), sm, st>>>(d, S1, h);
+    k<<<grid, NL * tpl_of<T, L>(), sm, st>>>(d, S1, h);
 }
 
 template <typename T, int L, int DIR> static void launch_py(const DemagDims& d, const typename Cplx<T>::type* in,
@@ -330,19 +623,141 @@ template <typename T, int L, int DIR> static void launch_py(const DemagDims& d, 
     dim3 grid((d.KX + B - 1) / B, (3 * d.nz + G - 1) / G);
     auto k = p_y_pass<T, L, B, G, DIR>;
     set_smem(k, sm);
-    k<<<grid, B * G * tpl_of<L>(), sm, st>>>(d, in, out);
+    k<<<grid, B * G * tpl_of<T, L>(), sm, st>>>(d, in, out);
+}
+
+// ---- tensor maps (driver entry point looked up once through the runtime) ----
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map over 8-byte elements (one float complex), dims innermost first
+static bool encode_3d(CUtensorMap* map, const void* base, const cuuint64_t dims[3], const cuuint64_t strides[2],
+                      const cuuint32_t box[3]) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename K> static int persistent_grid(K kernel, int threads, size_t smem, int work) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    const int g = sms * (occ > 0 ? occ : 1);
+    return work < g ? work : g;
+}
+
+// TMA y pass (FP32 only): returns false if it could not be used (caller falls back)
+// kx columns per TMA tile: two slots of L x B complex floats stay within 128 KB
+template <int L> constexpr int b_tma() { return (8192 / L) < 16 ? ((8192 / L) < 2 ? 2 : 8192 / L) : 16; }
+
+template <int L, int DIR>
+static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cudaStream_t st) {
+    constexpr int B = b_tma<L>();
+    using F = Fft<float, L, DIR, (DIR < 0 && L > 1)>;
+    const int rows_in = DIR < 0 ? d.ny : L;
+    if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
+    const int box_rows = rows_in < 256 ? rows_in : 256;
+    const int nboxes = (rows_in + box_rows - 1) / box_rows;
+    if ((size_t)nboxes * box_rows > (size_t)L) return false;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.KX, (cuuint64_t)rows_in, (cuuint64_t)(3 * d.nz)};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)rows_in * d.KXS * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)B, (cuuint32_t)box_rows, 1};
+    if (!encode_3d(&map, in, dims, strides, box)) return false;
+    const int threads = B * F::TPL;
+    const size_t sm = 2 * (size_t)L * B * sizeof(float2) + 16;
+    auto k = p_y_tma<float, L, B, DIR>;
+    set_smem(k, sm);
+    const int nkt = (d.KX + B - 1) / B;
+    const int grid = persistent_grid(k, threads, sm, nkt * 3 * d.nz);
+    k<<<grid, threads, sm, st>>>(d, map, out, box_rows, nboxes);
+    return true;
+}
+
+static bool encode_4d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, const cuuint64_t dims[4],
+                      const cuuint64_t strides[3], const cuuint32_t box[4]) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(map, dt, 4, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA z pass (FP32, Pz <= 256, nz <= 256): false if it cannot be used
+template <int L>
+static bool launch_p3_tma(const DemagDims& d, float2* S2, const float* tens, cudaStream_t st) {
+    constexpr int B = 16;
+    if (!d.err || (d.KXS * 8) % 16 != 0 || (d.KXS * 4) % 16 != 0 || d.nz > 256 || L / 2 + 1 > 256) return false;
+    if ((reinterpret_cast<uintptr_t>(S2) & 15) != 0 || (reinterpret_cast<uintptr_t>(tens) & 15) != 0) return false;
+    const int KY2 = d.LY / 2 + 1, KZ2 = L / 2 + 1;
+    CUtensorMap s2m, tm;
+    const cuuint64_t sd[4] = {(cuuint64_t)d.KX, (cuuint64_t)d.LY, (cuuint64_t)d.nz, 3};
+    const cuuint64_t ss[3] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)d.LY * d.KXS * 8, (cuuint64_t)d.nz * d.LY * d.KXS * 8};
+    const cuuint32_t sb[4] = {(cuuint32_t)B, 1, (cuuint32_t)d.nz, 3};
+    const cuuint64_t td[4] = {(cuuint64_t)d.KX, (cuuint64_t)KY2, (cuuint64_t)KZ2, 6};
+    const cuuint64_t ts[3] = {(cuuint64_t)d.KXS * 4, (cuuint64_t)KY2 * d.KXS * 4, (cuuint64_t)KZ2 * KY2 * d.KXS * 4};
+    const cuuint32_t tb[4] = {(cuuint32_t)B, 1, (cuuint32_t)KZ2, 6};
+    if (!encode_4d(&s2m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, S2, sd, ss, sb)) return false;
+    if (!encode_4d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tens, td, ts, tb)) return false;
+    const int s2_bytes = (int)((3 * (size_t)d.nz * B * sizeof(float2) + 127) / 128 * 128);
+    const int t_bytes = (int)((6 * (size_t)KZ2 * B * sizeof(float) + 127) / 128 * 128);
+    // the S2 part of a slot is also the transforms' scratch: L x B complex values
+    const int s2_area = s2_bytes > (int)(L * B * sizeof(float2)) ? s2_bytes : (int)(L * B * sizeof(float2));
+    const int slot_bytes = s2_area + t_bytes;
+    const size_t sm = 2 * (size_t)slot_bytes + 16;
+    auto k = p3_z_tma<L, B>;
+    set_smem(k, sm);
+    const int threads = B * Fft<float, L, -1, (L > 1)>::TPL;
+    const int nkt = (d.KX + B - 1) / B;
+    const int grid = persistent_grid(k, threads, sm, nkt * d.LY);
+    k<<<grid, threads, sm, st>>>(d, s2m, tm, S2, slot_bytes, s2_area);
+    return true;
 }
 
 template <typename T, int L> static void launch_p3(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens,
                                                    cudaStream_t st) {
     constexpr int B = b_of<T, L>(), G = g_of<T, L>();
     using C = typename Cplx<T>::type;
-    const size_t sm = 3 * (size_t)L * B * G * sizeof(C);
     const int kyi = 2 * (d.LY / 2 + 1);
     dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G);
-    auto k = p3_z_conv<T, L, B, G>;
-    set_smem(k, sm);
-    k<<<grid, B * G * tpl_of<L>(), sm, st>>>(d, S2, tens);
+    if constexpr (sizeof(T) == 4 && L <= 256) {
+        if (launch_p3_tma<L>(d, S2, tens, st)) return;
+        // 128-thread CTAs: three fit per SM at up to 170 registers per thread
+        constexpr int G3 = (B * tpl_of<T, L>() >= 128) ? 1 : 128 / (B * tpl_of<T, L>());
+        dim3 grid3((d.KX + B - 1) / B, (kyi + G3 - 1) / G3);
+        const size_t sm = (size_t)L * B * G3 * sizeof(C);
+        auto k = p3_z_conv_reg<T, L, B, G3>;
+        set_smem(k, sm);
+        k<<<grid3, B * G3 * tpl_of<T, L>(), sm, st>>>(d, S2, tens);
+    } else {
+        const size_t sm = 3 * (size_t)L * B * G * sizeof(C);
+        auto k = p3_z_conv<T, L, B, G>;
+        set_smem(k, sm);
+        k<<<grid, B * G * tpl_of<T, L>(), sm, st>>>(d, S2, tens);
+    }
+}
+
+template <typename T, int L, int DIR> static void launch_y(const DemagDims& d, const typename Cplx<T>::type* in,
+                                                           typename Cplx<T>::type* out, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && L >= 16) {
+        if (launch_py_tma<L, DIR>(d, in, out, st)) return;
+    }
+    launch_py<T, L, DIR>(d, in, out, st);
 }
 
 #define MM_DISPATCH_L(Lv, CALL)             \
@@ -374,7 +789,7 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
     tm->end(st);
     if (d.LY > 1) {
         tm->begin(st, "p2_y_forward");
-        MM_DISPATCH_L(d.LY, (launch_py<T, L_, -1>(d, S1, S2, st)));
+        MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
         tm->end(st);
     }
     tm->begin(st, "p3_z_conv");
@@ -382,7 +797,7 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
     tm->end(st);
     if (d.LY > 1) {
         tm->begin(st, "p4_y_inverse");
-        MM_DISPATCH_L(d.LY, (launch_py<T, L_, +1>(d, S2, S1, st)));
+        MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
         tm->end(st);
     }
     tm->begin(st, "p5_x_inverse");

@@ -19,6 +19,8 @@
 // __syncthreads()).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace mm {
@@ -31,6 +33,10 @@ struct FftLine {
     static constexpr int TPL = L >= 8 ? L / 8 : 1;
     static constexpr int R0 = (K <= 3) ? L : ((K % 3) ? (1 << (K % 3)) : 8);
     static constexpr int NPASS = (K <= 3) ? 1 : (K / 3 + ((K % 3) ? 1 : 0));
+
+    // element of the input that register r of thread j holds, and whether it can be nonzero
+    static __device__ __forceinline__ int in_index(int j, int r) { return j + r * TPL; }
+    static __host__ __device__ constexpr bool in_live(int r) { return !ZIN || L == 1 || r < NR / 2; }
 
     static __device__ __forceinline__ void run(C* v, C* s, int LS, int j) {
         if constexpr (L == 1) {
@@ -114,5 +120,127 @@ struct FftLine {
         }
     }
 };
+
+// Radix-16 variant (L >= 16): NR = 16 registers, TPL = L/16 threads per line,
+// plan R0 x 16^m with R0 = 2^(log2 L mod 4) (or 16).  The pattern layout and
+// the calling convention are those of FftLine, except that with ZIN and
+// R0 = 2 the first radix-2 pass (which only duplicates each input) is folded
+// into the load: register r then holds input element in_index(j, r) =
+// (j + r TPL) / 2 and one shared-memory exchange is saved.  Twiddles of a
+// radix-16 pass come from four table loads (w, w^2, w^4, w^8); the other
+// powers are at most three products away.
+template <typename T, int L, int DIR, bool ZIN>
+struct FftLine16 {
+    using C = typename Cplx<T>::type;
+    static_assert(L >= 16, "FftLine16 needs L >= 16");
+    static constexpr int K = ilog2(L);
+    static constexpr int NR = 16;
+    static constexpr int TPL = L / 16;
+    static constexpr int R0 = (K % 4) ? (1 << (K % 4)) : 16;
+    static constexpr int NPASS = (K % 4) ? (K / 4 + 1) : (K / 4);
+    static constexpr bool FOLD2 = ZIN && R0 == 2;
+
+    static __device__ __forceinline__ int in_index(int j, int r) { return FOLD2 ? ((j + r * TPL) >> 1) : (j + r * TPL); }
+    static __host__ __device__ constexpr bool in_live(int r) { return FOLD2 || !ZIN || r < 8; }
+
+    static __device__ __forceinline__ void twiddle16(C* v, int kidx) {
+        // v[r] *= W_L^(kidx r), r = 1..15
+        const C w1 = twiddle<T, L, DIR>(kidx & (L - 1));
+        const C w2 = twiddle<T, L, DIR>((2 * kidx) & (L - 1));
+        const C w4 = twiddle<T, L, DIR>((4 * kidx) & (L - 1));
+        const C w8 = twiddle<T, L, DIR>((8 * kidx) & (L - 1));
+        const C w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+        v[1] = cmul(v[1], w1); v[2] = cmul(v[2], w2); v[3] = cmul(v[3], w3); v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], w5); v[6] = cmul(v[6], w6); v[7] = cmul(v[7], w7); v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w1, w8)); v[10] = cmul(v[10], cmul(w2, w8)); v[11] = cmul(v[11], cmul(w3, w8));
+        v[12] = cmul(v[12], cmul(w4, w8)); v[13] = cmul(v[13], cmul(w5, w8)); v[14] = cmul(v[14], cmul(w6, w8));
+        v[15] = cmul(v[15], cmul(w7, w8));
+    }
+
+    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j) {
+        if constexpr (NPASS == 1) {
+            dft16<DIR, ZIN>(v);
+            return;
+        } else {
+            // ---- first pass (radix R0, span 1), unless folded into the load ----
+            if constexpr (!FOLD2) {
+                if constexpr (R0 == 16) {
+                    dft16<DIR, ZIN>(v);
+                    __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) s[(16 * j + q) * LS] = v[q];
+                } else if constexpr (R0 == 8) {
+                    __syncthreads();
+#pragma unroll
+                    for (int rr = 0; rr < 2; ++rr) {
+                        C a[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) a[q] = v[rr + 2 * q];
+                        if (ZIN) dft8_half<DIR>(a); else dft8<DIR>(a);
+                        const int b = j + rr * TPL;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s[(8 * b + q) * LS] = a[q];
+                    }
+                } else if constexpr (R0 == 4) {
+                    __syncthreads();
+#pragma unroll
+                    for (int rr = 0; rr < 4; ++rr) {
+                        C a0 = v[rr], a1 = v[rr + 4], a2, a3;
+                        if (ZIN) {
+                            a2 = csub(a0, a1);
+                            a3 = csub(a0, mul_i<DIR>(a1));
+                            C b1 = cadd(a0, mul_i<DIR>(a1));
+                            a0 = cadd(a0, a1);
+                            a1 = b1;
+                        } else {
+                            a2 = v[rr + 8];
+                            a3 = v[rr + 12];
+                            dft4<DIR>(a0, a1, a2, a3);
+                        }
+                        const int b = j + rr * TPL;
+                        s[(4 * b + 0) * LS] = a0;
+                        s[(4 * b + 1) * LS] = a1;
+                        s[(4 * b + 2) * LS] = a2;
+                        s[(4 * b + 3) * LS] = a3;
+                    }
+                } else {  // R0 == 2, not zero-padded
+                    __syncthreads();
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) {
+                        C a0 = v[rr], a1 = v[rr + 8];
+                        dft2<DIR>(a0, a1);
+                        const int b = j + rr * TPL;
+                        s[(2 * b + 0) * LS] = a0;
+                        s[(2 * b + 1) * LS] = a1;
+                    }
+                }
+            }
+            // ---- radix-16 passes ----
+#pragma unroll
+            for (int p = 1; p < NPASS; ++p) {
+                const int Ns = R0 << (4 * (p - 1));
+                if (!(FOLD2 && p == 1)) {
+                    __syncthreads();
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = s[(j + r * TPL) * LS];
+                }
+                const int k = j & (Ns - 1);
+                twiddle16(v, k * (L / (Ns * 16)));
+                dft16<DIR, false>(v);
+                if (p < NPASS - 1) {
+                    __syncthreads();
+                    const int idxD = (j / Ns) * Ns * 16 + k;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) s[(idxD + q * Ns) * LS] = v[q];
+                }
+            }
+        }
+    }
+};
+
+// engine choice: radix 16 for FP32 lines of 16+ points, radix 8 otherwise
+template <typename T, int L, int DIR, bool ZIN>
+using Fft = typename std::conditional<(sizeof(T) == 4 && L >= 16), FftLine16<T, L, DIR, ZIN>,
+                                      FftLine<T, L, DIR, ZIN>>::type;
 
 }  // namespace mm

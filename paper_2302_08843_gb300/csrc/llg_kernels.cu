@@ -50,6 +50,15 @@ template <> struct Vec<float, 4> {
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
 };
+template <> struct Vec<float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        v[0] = q.x; v[1] = q.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    }
+};
 template <> struct Vec<double, 2> {
     static __device__ __forceinline__ void ld(const double* p, double* v) {
         const double2 q = *reinterpret_cast<const double2*>(p);
@@ -69,8 +78,10 @@ constexpr int kBX = 64, kBY = 4;   // threads per block: 64 along x, 4 rows of y
 // 3-D launch: blockIdx.z = z, blockIdx.y * kBY + threadIdx.y = y,
 // (blockIdx.x * kBX + threadIdx.x) * VEC = first x of the thread's cells.
 // Requires nx % VEC == 0 (all of a thread's cells in one row).
-template <typename T, int VEC>
-__global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) {
+// UNI: Ms, A, Ku and alpha are uniform scalars (easy axes may still vary by
+// grain); the per-cell branches for material maps then compile away.
+template <typename T, int VEC, bool UNI>
+__global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> p) {
     using LV = Vec<T, VEC>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
@@ -85,8 +96,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
         T mx[VEC], my[VEC], mz[VEC];
         LV::ld(m + i, mx); LV::ld(m + N + i, my); LV::ld(m + 2 * N + i, mz);
         T Ms[VEC], A[VEC];
-        if (p.Ms_cell) LV::ld(p.Ms_cell + i, Ms); else { for (int v = 0; v < VEC; ++v) Ms[v] = p.Ms; }
-        if (p.A_cell) LV::ld(p.A_cell + i, A); else { for (int v = 0; v < VEC; ++v) A[v] = p.A; }
+        if (!UNI && p.Ms_cell) LV::ld(p.Ms_cell + i, Ms); else { for (int v = 0; v < VEC; ++v) Ms[v] = p.Ms; }
+        if (!UNI && p.A_cell) LV::ld(p.A_cell + i, A); else { for (int v = 0; v < VEC; ++v) A[v] = p.A; }
+        const bool a_cell = !UNI && p.A_cell;
         // exchange sums s = sum_links w_link / d^2 (m_nb - m_i), w_link the harmonic mean of A
         T sx[VEC], sy_[VEC], sz_[VEC];
 #pragma unroll
@@ -98,15 +110,15 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
             if (x > 0) {
                 T nbx, nby, nbz, Anb;
                 if (v > 0) { nbx = mx[v - 1]; nby = my[v - 1]; nbz = mz[v - 1]; Anb = A[v - 1]; }
-                else { nbx = m[i - 1]; nby = m[N + i - 1]; nbz = m[2 * N + i - 1]; Anb = p.A_cell ? p.A_cell[i - 1] : p.A; }
-                const T w = (p.A_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
+                else { nbx = m[i - 1]; nby = m[N + i - 1]; nbz = m[2 * N + i - 1]; Anb = a_cell ? p.A_cell[i - 1] : p.A; }
+                const T w = (a_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
                 sx[v] += w * (nbx - mx[v]); sy_[v] += w * (nby - my[v]); sz_[v] += w * (nbz - mz[v]);
             }
             if (x < nx - 1) {
                 T nbx, nby, nbz, Anb;
                 if (v < VEC - 1) { nbx = mx[v + 1]; nby = my[v + 1]; nbz = mz[v + 1]; Anb = A[v + 1]; }
-                else { nbx = m[i + VEC]; nby = m[N + i + VEC]; nbz = m[2 * N + i + VEC]; Anb = p.A_cell ? p.A_cell[i + VEC] : p.A; }
-                const T w = (p.A_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
+                else { nbx = m[i + VEC]; nby = m[N + i + VEC]; nbz = m[2 * N + i + VEC]; Anb = a_cell ? p.A_cell[i + VEC] : p.A; }
+                const T w = (a_cell ? harmonic(A[v], Anb) : p.A) * p.idx2;
                 sx[v] += w * (nbx - mx[v]); sy_[v] += w * (nby - my[v]); sz_[v] += w * (nbz - mz[v]);
             }
         }
@@ -115,9 +127,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
         if (COND) {                                                                       \
             T nbx[VEC], nby[VEC], nbz[VEC], Anb[VEC];                                     \
             LV::ld(m + i + (OFF), nbx); LV::ld(m + N + i + (OFF), nby); LV::ld(m + 2 * N + i + (OFF), nbz); \
-            if (p.A_cell) LV::ld(p.A_cell + i + (OFF), Anb);                              \
+            if (a_cell) LV::ld(p.A_cell + i + (OFF), Anb);                                \
             _Pragma("unroll") for (int v = 0; v < VEC; ++v) {                              \
-                const T w = (p.A_cell ? harmonic(A[v], Anb[v]) : p.A) * (ID2);            \
+                const T w = (a_cell ? harmonic(A[v], Anb[v]) : p.A) * (ID2);              \
                 sx[v] += w * (nbx[v] - mx[v]); sy_[v] += w * (nby[v] - my[v]); sz_[v] += w * (nbz[v] - mz[v]); \
             }                                                                             \
         }
@@ -127,9 +139,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
         MM_VLINK(z < nz - 1, sz, p.idz2)
 #undef MM_VLINK
         T Ku[VEC], al[VEC], zw[VEC], hdx[VEC], hdy[VEC], hdz[VEC];
-        if (p.Ku_cell) LV::ld(p.Ku_cell + i, Ku); else { for (int v = 0; v < VEC; ++v) Ku[v] = p.Ku; }
-        if (p.alpha_cell) LV::ld(p.alpha_cell + i, al); else { for (int v = 0; v < VEC; ++v) al[v] = p.alpha; }
-        if (p.zw) LV::ld(p.zw + i, zw); else { for (int v = 0; v < VEC; ++v) zw[v] = (T)1; }
+        if (!UNI && p.Ku_cell) LV::ld(p.Ku_cell + i, Ku); else { for (int v = 0; v < VEC; ++v) Ku[v] = p.Ku; }
+        if (!UNI && p.alpha_cell) LV::ld(p.alpha_cell + i, al); else { for (int v = 0; v < VEC; ++v) al[v] = p.alpha; }
+        if (!UNI && p.zw) LV::ld(p.zw + i, zw); else { for (int v = 0; v < VEC; ++v) zw[v] = (T)1; }
         if (p.hd) { LV::ld(p.hd + i, hdx); LV::ld(p.hd + N + i, hdy); LV::ld(p.hd + 2 * N + i, hdz); }
         else { for (int v = 0; v < VEC; ++v) { hdx[v] = 0; hdy[v] = 0; hdz[v] = 0; } }
         T kx[VEC], ky[VEC], kz[VEC];
@@ -138,17 +150,19 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
         for (int v = 0; v < VEC; ++v) {
             T hx = 0, hy = 0, hz = 0, hex = 0, hey = 0, hez = 0, hax = 0, hay = 0, haz = 0, hzx = 0, hzy = 0, hzz = 0;
             T hdxv = 0, hdyv = 0, hdzv = 0;
-            if (Ms[v] != (T)0) {
-                const T inv = (T)1 / Ms[v];
-                const T cex = (T)(2.0 / kMu0) * inv;
+            if (UNI || Ms[v] != (T)0) {
+                const bool uni = UNI || !p.Ms_cell;
+                const T inv = uni ? (T)0 : (T)1 / Ms[v];
+                const T cex = uni ? p.cex_u : (T)(2.0 / kMu0) * inv;
                 hex = cex * sx[v]; hey = cex * sy_[v]; hez = cex * sz_[v];
-                if (Ku[v] != (T)0) {
+                if (UNI ? (p.Ku != (T)0) : (Ku[v] != (T)0)) {
                     T ex = p.ex, ey = p.ey, ez = p.ez;
                     if (p.grain) {
                         const int gi = p.grain[i + v];
                         ex = p.axis_tab[3 * gi]; ey = p.axis_tab[3 * gi + 1]; ez = p.axis_tab[3 * gi + 2];
                     }
-                    const T c = (T)(2.0 / kMu0) * Ku[v] * inv * (ex * mx[v] + ey * my[v] + ez * mz[v]);
+                    const T ck = (UNI || (uni && !p.Ku_cell)) ? p.cani_u : (T)(2.0 / kMu0) * Ku[v] * (uni ? (T)1 / Ms[v] : inv);
+                    const T c = ck * (ex * mx[v] + ey * my[v] + ez * mz[v]);
                     hax = c * ex; hay = c * ey; haz = c * ez;
                 }
                 hzx = zw[v] * p.hx0; hzy = zw[v] * p.hy0; hzz = zw[v] * p.hz0;
@@ -158,7 +172,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(StageParams<T> p) 
                 hz = hdzv + hez + haz + hzz;
             }
             hxo[v] = hx; hyo[v] = hy; hzo[v] = hz;
-            const T gp = (T)(-kGamma) / ((T)1 + al[v] * al[v]);
+            const T gp = (!UNI && p.alpha_cell) ? (T)(-kGamma) / ((T)1 + al[v] * al[v]) : p.gp_u;
             const T cx = my[v] * hz - mz[v] * hy, cy = mz[v] * hx - mx[v] * hz, cz = mx[v] * hy - my[v] * hx;
             const T dx_ = my[v] * cz - mz[v] * cy, dy_ = mz[v] * cx - mx[v] * cz, dz_ = mx[v] * cy - my[v] * cx;
             kx[v] = gp * (cx + al[v] * dx_); ky[v] = gp * (cy + al[v] * dy_); kz[v] = gp * (cz + al[v] * dz_);
@@ -371,13 +385,26 @@ template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t s
     p.ckT = (T)p.ck;
     p.dtT = (T)p.dt;
     p.acc_bT = (T)p.acc_b;
+    // uniform-material constants, computed once in double
+    p.cex_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 / (double)p.Ms) : (T)0;
+    p.cani_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 * (double)p.Ku / (double)p.Ms) : (T)0;
+    p.gp_u = (T)(-kGamma / (1.0 + (double)p.alpha * (double)p.alpha));
     const int vec = all_aligned(p) ? stage_vec<T>(p.nx) : 1;
     dim3 block(kBX, kBY);
     dim3 grid((p.nx / vec + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, p.nz);
     *nblocks = (int)(grid.x * grid.y * grid.z);
-    if (vec == 1) stage_kernel<T, 1><<<grid, block, 0, st>>>(p);
-    else if constexpr (sizeof(T) == 4) stage_kernel<T, 4><<<grid, block, 0, st>>>(p);
-    else stage_kernel<T, 2><<<grid, block, 0, st>>>(p);
+    // uniform material needs Ms != 0 too (the Ms = 0 test is compiled away)
+    const bool uni = !p.Ms_cell && !p.A_cell && !p.Ku_cell && !p.alpha_cell && !p.zw && p.Ms != (T)0;
+    if (vec == 1) {
+        if (uni) stage_kernel<T, 1, true><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 1, false><<<grid, block, 0, st>>>(p);
+    } else if constexpr (sizeof(T) == 4) {
+        if (uni) stage_kernel<T, 4, true><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 4, false><<<grid, block, 0, st>>>(p);
+    } else {
+        if (uni) stage_kernel<T, 2, true><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 2, false><<<grid, block, 0, st>>>(p);
+    }
 }
 
 void launch_finalize(const double* partials, int nblocks, double* scalars, cudaStream_t st) {

@@ -163,6 +163,7 @@ struct mm_state {
     double* partials = nullptr;
     int part_cap = 0;
     double* scalars = nullptr;     // device kNPart
+    int* dev_err = nullptr;        // device error word written by bounded waits
     double* h_scalars = nullptr;   // pinned host kNPart
     // material and field
     double Ms = 0, A = 0, Ku = 0, alpha = 0, axis[3] = {1, 0, 0};
@@ -302,7 +303,10 @@ template <typename T> mm_status run_stage(mm_state* s, StageParams<T>& p, bool r
 
 mm_status read_scalars(mm_state* s) {
     MM_CUDA(cudaMemcpyAsync(s->h_scalars, s->scalars, sizeof(double) * kNPart, cudaMemcpyDeviceToHost, s->st));
+    int derr = 0;
+    MM_CUDA(cudaMemcpyAsync(&derr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
     MM_CUDA(cudaStreamSynchronize(s->st));
+    if (derr != 0) return fail(MM_ETIMEOUT, "a bounded device-side wait gave up (code %d)", derr);
     return MM_OK;
 }
 
@@ -517,12 +521,15 @@ mm_status mm_state_create(const mm_grid* grid, mm_precision precision, void* cud
     if ((st = dev_alloc(&s->S1, s1)) != MM_OK) return bail(st);
     if ((st = dev_alloc(&s->S2, s2)) != MM_OK) return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&s->scalars), sizeof(double) * kNPart)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&s->dev_err), sizeof(int))) != MM_OK) return bail(st);
+    s->d.err = s->dev_err;
     e = cudaMallocHost(reinterpret_cast<void**>(&s->h_scalars), sizeof(double) * kNPart);
     if (e != cudaSuccess) return bail(fail(MM_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
     // spectrum padding columns are never written by the passes; keep them defined
     e = cudaMemsetAsync(s->S1, 0, s1, s->st);
     if (e == cudaSuccess && s2) e = cudaMemsetAsync(s->S2, 0, s2, s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->hd, 0, v3, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->dev_err, 0, sizeof(int), s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return bail(fail(MM_ECUDA, "initialising buffers: %s", cudaGetErrorString(e)));
     *out = s;
@@ -535,7 +542,8 @@ void mm_state_destroy(mm_state* s) {
     cudaStreamSynchronize(s->st);
     void** bufs[] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd, &s->S1, &s->S2, &s->tens, &s->Ms_cell,
                      &s->A_cell, &s->Ku_cell, &s->alpha_cell, &s->axis_tab, reinterpret_cast<void**>(&s->grain),
-                     &s->zw, reinterpret_cast<void**>(&s->partials), reinterpret_cast<void**>(&s->scalars)};
+                     &s->zw, reinterpret_cast<void**>(&s->partials), reinterpret_cast<void**>(&s->scalars),
+                     reinterpret_cast<void**>(&s->dev_err)};
     for (void** b : bufs) dev_free(*b);
     for (int q = 0; q < 7; ++q) dev_free(s->K[q]);
     if (s->h_scalars) cudaFreeHost(s->h_scalars);

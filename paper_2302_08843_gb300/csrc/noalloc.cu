@@ -61,7 +61,7 @@ extern "C" mm_status mm_demag_noalloc(const mm_grid* grid, mm_precision precisio
         return err(MM_EINVAL, "mm_demag_noalloc: padded FFT extent above 4096");
     const int KX = LX / 2 + 1;
     // spectra rows use stride KX here (the layout of mm_demag_spectrum_host)
-    DemagDims d{grid->nx, grid->ny, grid->nz, LX, LY, LZ, KX, KX};
+    DemagDims d{grid->nx, grid->ny, grid->nz, LX, LY, LZ, KX, KX, nullptr};   // no error word: classic kernels
     const size_t csz = precision == MM_FP64 ? 2 * sizeof(double) : 2 * sizeof(float);
     const size_t s1 = 3 * csz * (size_t)grid->ny * grid->nz * KX;
     const size_t s2 = LY > 1 ? 3 * csz * (size_t)grid->nz * LY * KX : 0;
