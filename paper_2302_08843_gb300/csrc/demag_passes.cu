@@ -93,6 +93,180 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
     }
 }
 
+// ------------------------------------------------------ P1 / P5 (TMA) ----
+// Persistent x passes for FP32.  A tile is 2*NL consecutive rows ([c][z][y]
+// order); TMA brings the rows of the tile after next into the slot the
+// current tile has just been staged out of.  Staging writes the tile into the
+// engine's [x][line] work area (two real rows per complex line), which is
+// then the transform's exchange scratch and the post-processing buffer.
+template <int LX, int NL>
+__global__ void __launch_bounds__(NL * Fft<float, LX, -1, (LX > 1)>::TPL)
+p1_x_tma(DemagDims d, const __grid_constant__ CUtensorMap m_map, float Ms, float2* __restrict__ S1, int nxb,
+         int nboxes, int slot_bytes) {
+    using C = float2;
+    using F = Fft<float, LX, -1, (LX > 1)>;
+    constexpr int LS = NL + 1;
+    constexpr int NT = NL * F::TPL;
+    constexpr int XH = LX > 1 ? LX / 2 : 1;
+    constexpr int KXn = LX / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    const int tid = threadIdx.x;
+    const int line = tid % NL, j = tid / NL;
+    const long rows = 3L * d.ny * d.nz;
+    const int ntiles = (int)((rows + 2 * NL - 1) / (2 * NL));
+    C* work = reinterpret_cast<C*>(smtma + 2 * (size_t)slot_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes + (size_t)LX * LS * sizeof(C));
+    const int rowpitch = nboxes * nxb;       // floats per staged row (boxes side by side)
+    const uint32_t tx = (uint32_t)(nboxes * nxb * 2 * NL * sizeof(float));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int sl) {
+        float* dst = reinterpret_cast<float*>(smtma + (size_t)sl * slot_bytes);
+        mbar_arrive_expect_tx(&bar[sl], tx);
+        for (int b = 0; b < nboxes; ++b)
+            tma_load_3d(dst + (size_t)b * nxb * 2 * NL, &m_map, &bar[sl], b * nxb, t * 2 * NL, 0);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    }
+    int i = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
+        const int sl = i & 1;
+        const float* tile = reinterpret_cast<const float*>(smtma + (size_t)sl * slot_bytes);
+        const bool ok = mbar_wait_bounded(&bar[sl], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((i + 1) >> 1) & 1);
+            }
+            return;
+        }
+        // staging: box b holds rows x columns [b*nxb, (b+1)*nxb) as [row][xb]
+        for (int idx = tid; idx < NL * XH; idx += NT) {
+            const int l = idx / XH, x = idx - l * XH;
+            float a = 0.f, b = 0.f;
+            if (x < d.nx) {
+                const int bx = x / nxb, xo = x - bx * nxb;
+                const float* bb = tile + (size_t)bx * nxb * 2 * NL;
+                a = bb[(2 * l) * nxb + xo] * Ms;
+                b = bb[(2 * l + 1) * nxb + xo] * Ms;
+            }
+            work[x * LS + l] = mk<C>(a, b);
+        }
+        __syncthreads();   // slot consumed
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * gridDim.x, sl);
+        }
+        (void)rowpitch;
+        C v[F::NR];
+#pragma unroll
+        for (int r = 0; r < F::NR; ++r) v[r] = F::in_live(r) ? work[F::in_index(j, r) * LS + line] : mk<C>(0, 0);
+        F::run(v, work + line, LS, j);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < F::NR; ++r) work[(j + r * F::TPL) * LS + line] = v[r];
+        __syncthreads();
+        const long row0 = (long)t * 2 * NL;
+        for (int idx = tid; idx < NL * KXn; idx += NT) {
+            const int l = idx / KXn, k = idx - l * KXn;
+            const long ra = row0 + 2 * l, rb = ra + 1;
+            const C zk = work[k * LS + l];
+            const C zm = work[((LX - k) & (LX - 1)) * LS + l];
+            if (ra < rows) S1[ra * d.KXS + k] = mk<C>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            if (rb < rows) S1[rb * d.KXS + k] = mk<C>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        }
+        __syncthreads();   // work area free for the next tile's staging
+    }
+}
+
+template <int LX, int NL>
+__global__ void __launch_bounds__(NL * Fft<float, LX, +1, false>::TPL)
+p5_x_tma(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float* __restrict__ h, int kxb, int nboxes,
+         int slot_bytes) {
+    using C = float2;
+    using F = Fft<float, LX, +1, false>;
+    constexpr int LS = NL + 1;
+    constexpr int NT = NL * F::TPL;
+    constexpr int KXn = LX / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    const int tid = threadIdx.x;
+    const int line = tid % NL, j = tid / NL;
+    const long rows = 3L * d.ny * d.nz;
+    const int ntiles = (int)((rows + 2 * NL - 1) / (2 * NL));
+    C* work = reinterpret_cast<C*>(smtma + 2 * (size_t)slot_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes + (size_t)LX * LS * sizeof(C));
+    const uint32_t tx = (uint32_t)(nboxes * kxb * 2 * NL * sizeof(C));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int sl) {
+        C* dst = reinterpret_cast<C*>(smtma + (size_t)sl * slot_bytes);
+        mbar_arrive_expect_tx(&bar[sl], tx);
+        for (int b = 0; b < nboxes; ++b)
+            tma_load_3d(dst + (size_t)b * kxb * 2 * NL, &s1_map, &bar[sl], b * kxb, t * 2 * NL, 0);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    }
+    int i = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
+        const int sl = i & 1;
+        const C* tile = reinterpret_cast<const C*>(smtma + (size_t)sl * slot_bytes);
+        const bool ok = mbar_wait_bounded(&bar[sl], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((i + 1) >> 1) & 1);
+            }
+            return;
+        }
+        for (int idx = tid; idx < NL * KXn; idx += NT) {
+            const int l = idx / KXn, k = idx - l * KXn;
+            const int bk = k / kxb, ko = k - bk * kxb;
+            const C* bb = tile + (size_t)bk * kxb * 2 * NL;
+            C A = bb[(2 * l) * kxb + ko], Bv = bb[(2 * l + 1) * kxb + ko];
+            if (k == 0 || 2 * k == LX) { A.y = 0.f; Bv.y = 0.f; }
+            work[k * LS + l] = mk<C>(A.x - Bv.y, A.y + Bv.x);
+            if (k > 0 && 2 * k < LX) work[(LX - k) * LS + l] = mk<C>(A.x + Bv.y, Bv.x - A.y);
+        }
+        __syncthreads();   // slot consumed
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * gridDim.x, sl);
+        }
+        C v[F::NR];
+#pragma unroll
+        for (int r = 0; r < F::NR; ++r) v[r] = work[(j + r * F::TPL) * LS + line];
+        F::run(v, work + line, LS, j);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < F::NR; ++r)
+            if (LX == 1 || r < F::NR / 2) work[(j + r * F::TPL) * LS + line] = v[r];
+        __syncthreads();
+        const long row0 = (long)t * 2 * NL;
+        for (int idx = tid; idx < NL * d.nx; idx += NT) {
+            const int l = idx / d.nx, x = idx - l * d.nx;
+            const long ra = row0 + 2 * l, rb = ra + 1;
+            const C z = work[x * LS + l];
+            if (ra < rows) h[ra * d.nx + x] = z.x;
+            if (rb < rows) h[rb * d.nx + x] = z.y;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- P2 / P4 ----
 // DIR = -1: S1 (ny rows) -> S2 (Py rows), forward, zero upper half.
 // DIR = +1: S2 (Py rows) -> S1 (ny rows), inverse, keep the lower half.
@@ -729,6 +903,70 @@ static bool launch_p3_tma(const DemagDims& d, float2* S2, const float* tens, cud
     return true;
 }
 
+// widest multiple of 8 elements <= 256 that covers n in the fewest boxes
+static int box_width(int n, int* nboxes) {
+    const int nb = (n + 255) / 256;
+    int w = (n + nb - 1) / nb;
+    w = (w + 7) / 8 * 8;
+    *nboxes = (n + w - 1) / w;
+    return w;
+}
+
+template <int L> static bool launch_p1_tma(const DemagDims& d, const float* m, const float* Ms_cell, float Ms,
+                                           float2* S1, cudaStream_t st) {
+    constexpr int NL = nl_x<float, L>();
+    if (!d.err || Ms_cell || L < 16 || (d.nx * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(m) & 15) != 0) return false;
+    if (2 * NL > 256) return false;
+    int nb = 0;
+    const int w = box_width(d.nx, &nb);
+    const long rows = 3L * d.ny * d.nz;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)rows, 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)rows * d.nx * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)(2 * NL), 1};
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(m), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const int slot_bytes = (int)(((size_t)nb * w * 2 * NL * sizeof(float) + 127) / 128 * 128);
+    const size_t sm = 2 * (size_t)slot_bytes + (size_t)L * (NL + 1) * sizeof(float2) + 16;
+    if (sm > 200 * 1024) return false;
+    auto k = p1_x_tma<L, NL>;
+    set_smem(k, sm);
+    const int threads = NL * Fft<float, L, -1, (L > 1)>::TPL;
+    const int ntiles = (int)((rows + 2 * NL - 1) / (2 * NL));
+    const int grid = persistent_grid(k, threads, sm, ntiles);
+    k<<<grid, threads, sm, st>>>(d, map, Ms, S1, w, nb, slot_bytes);
+    return true;
+}
+
+template <int L> static bool launch_p5_tma(const DemagDims& d, const float2* S1, float* h, cudaStream_t st) {
+    constexpr int NL = nl_x<float, L>();
+    if (!d.err || L < 16 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
+    if (2 * NL > 256) return false;
+    int nb = 0;
+    const int w = box_width(d.KX, &nb);
+    const long rows = 3L * d.ny * d.nz;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.KX, (cuuint64_t)rows, 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)rows * d.KXS * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)(2 * NL), 1};
+    if (!encode_3d(&map, S1, dims, strides, box)) return false;
+    const int slot_bytes = (int)(((size_t)nb * w * 2 * NL * sizeof(float2) + 127) / 128 * 128);
+    const size_t sm = 2 * (size_t)slot_bytes + (size_t)L * (NL + 1) * sizeof(float2) + 16;
+    if (sm > 200 * 1024) return false;
+    auto k = p5_x_tma<L, NL>;
+    set_smem(k, sm);
+    const int threads = NL * Fft<float, L, +1, false>::TPL;
+    const int ntiles = (int)((rows + 2 * NL - 1) / (2 * NL));
+    const int grid = persistent_grid(k, threads, sm, ntiles);
+    k<<<grid, threads, sm, st>>>(d, map, h, w, nb, slot_bytes);
+    return true;
+}
+
 template <typename T, int L> static void launch_p3(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens,
                                                    cudaStream_t st) {
     constexpr int B = b_of<T, L>(), G = g_of<T, L>();
@@ -760,6 +998,22 @@ template <typename T, int L, int DIR> static void launch_y(const DemagDims& d, c
     launch_py<T, L, DIR>(d, in, out, st);
 }
 
+template <typename T, int L> static void launch_x_fwd(const DemagDims& d, const T* m, const T* Ms_cell, T Ms,
+                                                      typename Cplx<T>::type* S1, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && L >= 16) {
+        if (launch_p1_tma<L>(d, m, Ms_cell, Ms, S1, st)) return;
+    }
+    launch_p1<T, L>(d, m, Ms_cell, Ms, S1, st);
+}
+
+template <typename T, int L> static void launch_x_inv(const DemagDims& d, const typename Cplx<T>::type* S1, T* h,
+                                                      cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && L >= 16) {
+        if (launch_p5_tma<L>(d, S1, h, st)) return;
+    }
+    launch_p5<T, L>(d, S1, h, st);
+}
+
 #define MM_DISPATCH_L(Lv, CALL)             \
     switch (Lv) {                           \
         case 1: { constexpr int L_ = 1; CALL; } break;       \
@@ -785,7 +1039,7 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
     // With ny == 1 the y passes are the identity and S2 aliases S1.
     C* S2e = d.LY == 1 ? S1 : S2;
     tm->begin(st, "p1_x_forward");
-    MM_DISPATCH_L(d.LX, (launch_p1<T, L_>(d, m, Ms_cell, Ms, S1, st)));
+    MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
     tm->end(st);
     if (d.LY > 1) {
         tm->begin(st, "p2_y_forward");
@@ -801,7 +1055,7 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
         tm->end(st);
     }
     tm->begin(st, "p5_x_inverse");
-    MM_DISPATCH_L(d.LX, (launch_p5<T, L_>(d, S1, h, st)));
+    MM_DISPATCH_L(d.LX, (launch_x_inv<T, L_>(d, S1, h, st)));
     tm->end(st);
 }
 
