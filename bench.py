@@ -62,7 +62,11 @@ def kernel_bytes(n, s, grains=True, ms_cell=False):
     # stage kernel of RK4, averaged over the four stages:
     # reads m_s, h_demag, m_n (all stages), acc (stages 2-4), grain ids; writes acc (1-3), next (all)
     stage = (4 * (3 * v3 + g + mc) + 3 * v3 + 3 * v3 + 4 * v3) / 4.0
+    # fused x-inverse + stage + x-forward: reads S1, m_s, m_n, grain ids, acc (3 of 4 stages);
+    # writes acc (3 of 4), next and S1
+    k5 = S1 + (4 * (3 * v3 + g) + 3 * v3 + 3 * v3 + 4 * v3) / 4.0 + S1
     return {
+        "k5_fused": k5,
         "p1_x_forward": v3 + mc + S1,
         "p2_y_forward": S1 + S2,
         "p3_z_conv": 2 * S2 + tens,

@@ -39,6 +39,11 @@ template <typename T>
 void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typename Cplx<T>::type* S1,
                  typename Cplx<T>::type* S2, const T* tens, T* h, cudaStream_t st, KernelTimer* tm);
 
+// P1 (optional) .. P4: leaves the x-spectrum of h in S1
+template <typename T>
+void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
+                 typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm);
+
 // number of doubles per block in the reduction partials
 constexpr int kNPart = 8;
 // partial / scalar slots
@@ -82,6 +87,12 @@ struct StageParams {
 };
 
 template <typename T> void launch_stage(const StageParams<T>& p, cudaStream_t st, int* nblocks);
+// fused x-inverse + stage + x-forward of the next stage input (FP32, uniform material, RK stages);
+// the coefficients in the field type (kcT, ckT, dtT, acc_bT) and the uniform constants must be filled
+bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st, KernelTimer* tm);
+bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p);
+// fill kcT, ckT, dtT, acc_bT and the uniform-material constants from the double fields
+template <typename T> void stage_prepare(StageParams<T>& p);
 template <typename T> int stage_blocks(int nx, int ny, int nz);   // blocks launch_stage will use
 void launch_finalize(const double* partials, int nblocks, double* scalars, cudaStream_t st);
 template <typename T> void launch_convert(const double* src, T* dst, long n, cudaStream_t st);

@@ -267,6 +267,233 @@ p5_x_tma(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float* __restr
     }
 }
 
+// ---------------------------------------------------------- fused K5 ----
+// x-inverse of the demag spectrum + exchange, anisotropy, Zeeman, LLG and the
+// RK combination + x-forward of Ms * (next stage input), for FP32 with a
+// uniform material (easy axes may vary by grain).  A tile is TY rows of y at
+// one z, all three components (3*TY real rows = 3*TY/2 complex lines, pairs of
+// consecutive y of one component); TMA fetches the tile after next.  After the
+// inverse transform the demag field sits in the [x][line] work area; each cell
+// update reads it there, writes acc/next to global memory and puts Ms * next
+// back in the same place, which the forward transform then turns into the
+// next stage's x-spectrum, written over this tile's rows of S1.
+template <int LX, int TY>
+__global__ void __launch_bounds__((3 * TY / 2) * Fft<float, LX, +1, false>::TPL, 2)
+k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __restrict__ S1, StageParams<float> p,
+         int kxb, int nboxes, int slot_bytes) {
+    using C = float2;
+    using FI = Fft<float, LX, +1, false>;
+    using FF = Fft<float, LX, -1, (LX > 1)>;
+    static_assert(FI::TPL == FF::TPL, "engines must agree on threads per line");
+    constexpr int NL = 3 * TY / 2;
+    constexpr int LS = NL + 1;
+    constexpr int NT = NL * FI::TPL;
+    constexpr int KXn = LX / 2 + 1;
+    constexpr int XH = LX / 2;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    const int tid = threadIdx.x;
+    const int line = tid % NL, j = tid / NL;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int N = nx * ny * nz;
+    const int nyt = (ny + TY - 1) / TY;
+    const int ntiles = nyt * nz;
+    C* work = reinterpret_cast<C*>(smtma + 2 * (size_t)slot_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes + (size_t)LX * LS * sizeof(C));
+    const uint32_t tx = (uint32_t)(nboxes * kxb * TY * 3 * sizeof(C));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int sl) {
+        const int yt = t % nyt, z = t / nyt;
+        C* dst = reinterpret_cast<C*>(smtma + (size_t)sl * slot_bytes);
+        mbar_arrive_expect_tx(&bar[sl], tx);
+        for (int b = 0; b < nboxes; ++b)
+            tma_load_4d(dst + (size_t)b * kxb * TY * 3, &s1_map, &bar[sl], b * kxb, yt * TY, z, 0);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    }
+    const float* m = p.m;
+    int it = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++it) {
+        const int sl = it & 1;
+        const C* tile = reinterpret_cast<const C*>(smtma + (size_t)sl * slot_bytes);   // [box][c][y][kx]
+        const bool ok = mbar_wait_bounded(&bar[sl], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int yt = t % nyt, z = t / nyt;
+        const int y0 = yt * TY;
+        // ---- stage the c2r input: line l = (c, q) pairs rows y0+2q, y0+2q+1 of component c
+        for (int idx = tid; idx < NL * KXn; idx += NT) {
+            const int l = idx / KXn, k = idx - l * KXn;
+            const int c = l / (TY / 2), q = l - c * (TY / 2);
+            const int bk = k / kxb, ko = k - bk * kxb;
+            const C* bb = tile + (size_t)bk * kxb * TY * 3;
+            C A = bb[(c * TY + 2 * q) * kxb + ko], Bv = bb[(c * TY + 2 * q + 1) * kxb + ko];
+            if (k == 0 || 2 * k == LX) { A.y = 0.f; Bv.y = 0.f; }
+            work[k * LS + l] = mk<C>(A.x - Bv.y, A.y + Bv.x);
+            if (k > 0 && 2 * k < LX) work[(LX - k) * LS + l] = mk<C>(A.x + Bv.y, Bv.x - A.y);
+        }
+        __syncthreads();   // slot consumed
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(t + 2 * gridDim.x, sl);
+        }
+        {
+            C v[FI::NR];
+#pragma unroll
+            for (int r = 0; r < FI::NR; ++r) v[r] = work[(j + r * FI::TPL) * LS + line];
+            FI::run(v, work + line, LS, j);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < FI::NR / 2; ++r) work[(j + r * FI::TPL) * LS + line] = v[r];
+        }
+        __syncthreads();
+        // ---- cell updates: two consecutive x cells per item, float2 loads
+        const int rows_here = (ny - y0) < TY ? (ny - y0) : TY;
+        for (int idx = tid; idx < TY * (XH / 2); idx += NT) {
+            const int yy = idx / (XH / 2), x0 = (idx - yy * (XH / 2)) * 2;
+            const int l0 = yy >> 1, part = yy & 1;     // line of component c is c*TY/2 + l0
+            float* w0 = reinterpret_cast<float*>(&work[x0 * LS + 0 * (TY / 2) + l0]) + part;
+            float* w1 = reinterpret_cast<float*>(&work[x0 * LS + 1 * (TY / 2) + l0]) + part;
+            float* w2 = reinterpret_cast<float*>(&work[x0 * LS + 2 * (TY / 2) + l0]) + part;
+            constexpr int WS = 2 * LS;                 // floats between x and x+1 in the work area
+            if (yy >= rows_here || x0 >= nx) {         // zero-padded inputs of the forward transform
+                w0[0] = 0.f; w1[0] = 0.f; w2[0] = 0.f;
+                w0[WS] = 0.f; w1[WS] = 0.f; w2[WS] = 0.f;
+                continue;
+            }
+            const int y = y0 + yy;
+            const int i = x0 + nx * (y + ny * z);      // even: float2 aligned (nx even)
+            const float2* m2 = reinterpret_cast<const float2*>(m);
+            const int i2 = i >> 1, N2 = N >> 1;
+            const float2 cx2 = m2[i2], cy2 = m2[N2 + i2], cz2 = m2[2 * N2 + i2];
+            const float mxv[2] = {cx2.x, cx2.y}, myv[2] = {cy2.x, cy2.y}, mzv[2] = {cz2.x, cz2.y};
+            float sx[2] = {0.f, 0.f}, sy[2] = {0.f, 0.f}, sz[2] = {0.f, 0.f};
+            {   // x links
+                const float wx = p.A * p.idx2;
+                // inner link between the two cells
+                sx[0] += wx * (mxv[1] - mxv[0]); sy[0] += wx * (myv[1] - myv[0]); sz[0] += wx * (mzv[1] - mzv[0]);
+                sx[1] += wx * (mxv[0] - mxv[1]); sy[1] += wx * (myv[0] - myv[1]); sz[1] += wx * (mzv[0] - mzv[1]);
+                if (x0 > 0) {
+                    sx[0] += wx * (m[i - 1] - mxv[0]); sy[0] += wx * (m[N + i - 1] - myv[0]);
+                    sz[0] += wx * (m[2 * N + i - 1] - mzv[0]);
+                }
+                if (x0 + 2 < nx) {
+                    sx[1] += wx * (m[i + 2] - mxv[1]); sy[1] += wx * (m[N + i + 2] - myv[1]);
+                    sz[1] += wx * (m[2 * N + i + 2] - mzv[1]);
+                }
+            }
+#define MM_F2LINK(COND, OFF2, ID2)                                                             \
+            if (COND) {                                                                        \
+                const float w = p.A * (ID2);                                                   \
+                const float2 a = m2[i2 + (OFF2)], b = m2[N2 + i2 + (OFF2)], c = m2[2 * N2 + i2 + (OFF2)]; \
+                sx[0] += w * (a.x - mxv[0]); sy[0] += w * (b.x - myv[0]); sz[0] += w * (c.x - mzv[0]); \
+                sx[1] += w * (a.y - mxv[1]); sy[1] += w * (b.y - myv[1]); sz[1] += w * (c.y - mzv[1]); \
+            }
+            MM_F2LINK(y > 0, -(nx >> 1), p.idy2)
+            MM_F2LINK(y < ny - 1, (nx >> 1), p.idy2)
+            MM_F2LINK(z > 0, -((nx * ny) >> 1), p.idz2)
+            MM_F2LINK(z < nz - 1, ((nx * ny) >> 1), p.idz2)
+#undef MM_F2LINK
+            const float2 n0 = reinterpret_cast<const float2*>(p.mn)[i2];
+            const float2 n1 = reinterpret_cast<const float2*>(p.mn)[N2 + i2];
+            const float2 n2 = reinterpret_cast<const float2*>(p.mn)[2 * N2 + i2];
+            const float mnx[2] = {n0.x, n0.y}, mny[2] = {n1.x, n1.y}, mnz[2] = {n2.x, n2.y};
+            float ax_[2] = {0.f, 0.f}, ay_[2] = {0.f, 0.f}, az_[2] = {0.f, 0.f};
+            const float* accsrc = p.acc_in ? p.acc_in : (p.nk > 0 ? p.kin[0] : nullptr);
+            if (accsrc) {
+                const float2 a0 = reinterpret_cast<const float2*>(accsrc)[i2];
+                const float2 a1 = reinterpret_cast<const float2*>(accsrc)[N2 + i2];
+                const float2 a2 = reinterpret_cast<const float2*>(accsrc)[2 * N2 + i2];
+                ax_[0] = a0.x; ax_[1] = a0.y; ay_[0] = a1.x; ay_[1] = a1.y; az_[0] = a2.x; az_[1] = a2.y;
+            }
+            float ox[2], oy[2], oz[2], accx[2], accy[2], accz[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const float mx = mxv[v], my = myv[v], mz = mzv[v];
+                float hx = p.cex_u * sx[v], hy = p.cex_u * sy[v], hz = p.cex_u * sz[v];
+                if (p.Ku != 0.f) {
+                    float ex = p.ex, ey = p.ey, ez = p.ez;
+                    if (p.grain) {
+                        const int gi = p.grain[i + v];
+                        ex = p.axis_tab[3 * gi]; ey = p.axis_tab[3 * gi + 1]; ez = p.axis_tab[3 * gi + 2];
+                    }
+                    const float c = p.cani_u * (ex * mx + ey * my + ez * mz);
+                    hx += c * ex; hy += c * ey; hz += c * ez;
+                }
+                hx += w0[v * WS] + p.hx0;
+                hy += w1[v * WS] + p.hy0;
+                hz += w2[v * WS] + p.hz0;
+                const float al = p.alpha, gp = p.gp_u;
+                const float cx = my * hz - mz * hy, cy = mz * hx - mx * hz, cz = mx * hy - my * hx;
+                const float dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
+                const float kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
+                // RK combination: acc_out = acc_in + acc_b k;  next = mn + dt (kc0 kin0 + ck k)
+                accx[v] = p.acc_bT * kx + (p.acc_in ? ax_[v] : 0.f);
+                accy[v] = p.acc_bT * ky + (p.acc_in ? ay_[v] : 0.f);
+                accz[v] = p.acc_bT * kz + (p.acc_in ? az_[v] : 0.f);
+                const float c0 = p.nk > 0 ? p.kcT[0] : 0.f;
+                float a = mnx[v] + p.dtT * (p.ckT * kx + c0 * ax_[v]);
+                float b = mny[v] + p.dtT * (p.ckT * ky + c0 * ay_[v]);
+                float c = mnz[v] + p.dtT * (p.ckT * kz + c0 * az_[v]);
+                if (p.renorm) {
+                    const float nn = a * a + b * b + c * c;
+                    if (nn > 0.f) {
+                        const float sc = 1.f / sqrtf(nn);
+                        a *= sc; b *= sc; c *= sc;
+                    }
+                }
+                ox[v] = a; oy[v] = b; oz[v] = c;
+                // Ms * next for the forward transform (the demag values at this place are consumed)
+                w0[v * WS] = p.Ms * a; w1[v * WS] = p.Ms * b; w2[v * WS] = p.Ms * c;
+            }
+            if (p.acc_out) {
+                float2* ao = reinterpret_cast<float2*>(p.acc_out);
+                ao[i2] = make_float2(accx[0], accx[1]);
+                ao[N2 + i2] = make_float2(accy[0], accy[1]);
+                ao[2 * N2 + i2] = make_float2(accz[0], accz[1]);
+            }
+            float2* no = reinterpret_cast<float2*>(p.next);
+            no[i2] = make_float2(ox[0], ox[1]);
+            no[N2 + i2] = make_float2(oy[0], oy[1]);
+            no[2 * N2 + i2] = make_float2(oz[0], oz[1]);
+        }
+        __syncthreads();
+        // ---- forward transform of Ms * next and the real-pair post-processing
+        {
+            C v[FF::NR];
+#pragma unroll
+            for (int r = 0; r < FF::NR; ++r) v[r] = FF::in_live(r) ? work[FF::in_index(j, r) * LS + line] : mk<C>(0, 0);
+            FF::run(v, work + line, LS, j);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < FF::NR; ++r) work[(j + r * FF::TPL) * LS + line] = v[r];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NL * KXn; idx += NT) {
+            const int l = idx / KXn, k = idx - l * KXn;
+            const int c = l / (TY / 2), q = l - c * (TY / 2);
+            const int ya = y0 + 2 * q, yb = ya + 1;
+            const C zk = work[k * LS + l];
+            const C zm = work[((LX - k) & (LX - 1)) * LS + l];
+            if (ya < ny) S1[((long)(c * nz + z) * ny + ya) * d.KXS + k] = mk<C>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            if (yb < ny) S1[((long)(c * nz + z) * ny + yb) * d.KXS + k] = mk<C>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        }
+        __syncthreads();   // work area free for the next tile
+    }
+}
+
 // ------------------------------------------------------------- P2 / P4 ----
 // DIR = -1: S1 (ny rows) -> S2 (Py rows), forward, zero upper half.
 // DIR = +1: S2 (Py rows) -> S1 (ny rows), inverse, keep the lower half.
@@ -1014,6 +1241,40 @@ template <typename T, int L> static void launch_x_inv(const DemagDims& d, const 
     launch_p5<T, L>(d, S1, h, st);
 }
 
+// fused K5 launcher (see k5_fused): false if the shape or material does not qualify
+template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st) {
+    constexpr int TY = 4;
+    if constexpr (L < 16) {
+        return false;
+    } else {
+        if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
+        if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.Ms == 0.f || p.hd || p.k_out ||
+            p.h_out || p.want_err || p.want_energy || p.want_torque || !p.next || p.nk > 1)
+            return false;
+        if (d.nx % 2 != 0) return false;
+        int nb = 0;
+        const int w = box_width(d.KX, &nb);
+        CUtensorMap map;
+        const cuuint64_t dims[4] = {(cuuint64_t)d.KX, (cuuint64_t)d.ny, (cuuint64_t)d.nz, 3};
+        const cuuint64_t strides[3] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)d.ny * d.KXS * 8,
+                                       (cuuint64_t)d.nz * d.ny * d.KXS * 8};
+        const cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)TY, 1, 3};
+        if (!encode_4d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, S1, dims, strides, box)) return false;
+        constexpr int NL = 3 * TY / 2;
+        const int slot_bytes = (int)(((size_t)nb * w * TY * 3 * sizeof(float2) + 127) / 128 * 128);
+        const size_t sm = 2 * (size_t)slot_bytes + (size_t)L * (NL + 1) * sizeof(float2) + 16;
+        if (sm > 220 * 1024) return false;
+        auto k = k5_fused<L, TY>;
+        set_smem(k, sm);
+        const int threads = NL * Fft<float, L, +1, false>::TPL;
+        if (threads > 1024) return false;
+        const int ntiles = ((d.ny + TY - 1) / TY) * d.nz;
+        const int grid = persistent_grid(k, threads, sm, ntiles);
+        k<<<grid, threads, sm, st>>>(d, map, S1, p, w, nb, slot_bytes);
+        return true;
+    }
+}
+
 #define MM_DISPATCH_L(Lv, CALL)             \
     switch (Lv) {                           \
         case 1: { constexpr int L_ = 1; CALL; } break;       \
@@ -1058,6 +1319,51 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
     MM_DISPATCH_L(d.LX, (launch_x_inv<T, L_>(d, S1, h, st)));
     tm->end(st);
 }
+
+template <typename T>
+void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
+                 typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm) {
+    using C = typename Cplx<T>::type;
+    C* S2e = d.LY == 1 ? S1 : S2;
+    if (need_p1) {
+        tm->begin(st, "p1_x_forward");
+        MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
+        tm->end(st);
+    }
+    if (d.LY > 1) {
+        tm->begin(st, "p2_y_forward");
+        MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
+        tm->end(st);
+    }
+    tm->begin(st, "p3_z_conv");
+    MM_DISPATCH_L(d.LZ, (launch_p3<T, L_>(d, S2e, tens, st)));
+    tm->end(st);
+    if (d.LY > 1) {
+        tm->begin(st, "p4_y_inverse");
+        MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
+        tm->end(st);
+    }
+}
+
+bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st, KernelTimer* tm) {
+    bool ok = false;
+    tm->begin(st, "k5_fused");
+    MM_DISPATCH_L(d.LX, (ok = launch_k5<L_>(d, S1, p, st)));
+    tm->end(st);
+    return ok;
+}
+
+bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
+    if (!d.err || d.LX < 16 || d.LX > 4096 || d.nx % 2 != 0) return false;
+    if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.Ms == 0.f) return false;
+    const int threads = 6 * (d.LX / 16);
+    return threads <= 1024;
+}
+
+template void demag_front<float>(const DemagDims&, const float*, const float*, float, bool, float2*, float2*,
+                                 const float*, cudaStream_t, KernelTimer*);
+template void demag_front<double>(const DemagDims&, const double*, const double*, double, bool, double2*, double2*,
+                                  const double*, cudaStream_t, KernelTimer*);
 
 template void demag_apply<float>(const DemagDims&, const float*, const float*, float, float2*, float2*,
                                  const float*, float*, cudaStream_t, KernelTimer*);

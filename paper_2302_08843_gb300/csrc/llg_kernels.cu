@@ -379,8 +379,7 @@ template <typename T> static bool all_aligned(const StageParams<T>& p) {
     return true;
 }
 
-template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t st, int* nblocks) {
-    StageParams<T> p = p0;
+template <typename T> void stage_prepare(StageParams<T>& p) {
     for (int q = 0; q < 7; ++q) p.kcT[q] = (T)p.kc[q];
     p.ckT = (T)p.ck;
     p.dtT = (T)p.dt;
@@ -389,6 +388,13 @@ template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t s
     p.cex_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 / (double)p.Ms) : (T)0;
     p.cani_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 * (double)p.Ku / (double)p.Ms) : (T)0;
     p.gp_u = (T)(-kGamma / (1.0 + (double)p.alpha * (double)p.alpha));
+}
+template void stage_prepare<float>(StageParams<float>&);
+template void stage_prepare<double>(StageParams<double>&);
+
+template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t st, int* nblocks) {
+    StageParams<T> p = p0;
+    stage_prepare(p);
     const int vec = all_aligned(p) ? stage_vec<T>(p.nx) : 1;
     dim3 block(kBX, kBY);
     dim3 grid((p.nx / vec + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, p.nz);

@@ -172,6 +172,8 @@ struct mm_state {
     void* user = nullptr;
     bool have_m = false, have_mat = false, demag_ready = false, demag_off = false;
     bool fsal = false;
+    bool s1_fresh = false;   // S1 holds the x-spectrum of Ms m for the current m (left by the fused RK4 path)
+    bool use_fused = true;   // RK4 in FP32 may take the fused stage kernel
     KernelTimer timer;
 };
 
@@ -271,6 +273,7 @@ template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, con
 
 // demag field of m into s->hd
 template <typename T> mm_status run_demag(mm_state* s, const void* m) {
+    s->s1_fresh = false;
     if (s->demag_off) return MM_OK;
     using C = typename Cplx<T>::type;
     demag_apply<T>(s->d, (const T*)m, (const T*)s->Ms_cell, (T)s->Ms, (C*)s->S1, (C*)s->S2, (const T*)s->tens,
@@ -334,7 +337,58 @@ mm_status heff_impl(mm_state* s, const void* m, void* h_out, double* E_out, doub
 
 const double kRK4_C[4] = {0.0, 0.5, 0.5, 1.0};
 
+// RK4 through the fused x-inverse + stage + x-forward kernel (FP32, uniform material)
+mm_status rk4_fused(mm_state* s, double dt, double t, bool* used) {
+    *used = false;
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double anext[3] = {0.5, 0.5, 1.0};
+    void* in[4] = {s->m, s->mA, s->mB, s->mA};
+    void* out[4] = {s->m, s->mA, s->mB, s->mA};
+    out[0] = s->mA; out[1] = s->mB; out[2] = s->mA; out[3] = s->m;
+    StageParams<float> probe;
+    fill_common<float>(s, probe, s->m, t);
+    if (s->demag_off || !s->demag_ready || !fused_stage_supported(s->d, probe)) return MM_OK;
+    for (int st = 0; st < 4; ++st) {
+        demag_front<float>(s->d, (const float*)in[st], (const float*)s->Ms_cell, (float)s->Ms,
+                           st == 0 && !s->s1_fresh, (float2*)s->S1, (float2*)s->S2, (const float*)s->tens, s->st,
+                           &s->timer);
+        MM_LAUNCHED();
+        StageParams<float> p;
+        fill_common<float>(s, p, in[st], t + kRK4_C[st] * dt);
+        p.hd = nullptr;
+        p.dt = dt;
+        p.next = (float*)out[st];
+        if (st < 3) {
+            p.acc_in = st == 0 ? nullptr : (const float*)s->acc;
+            p.acc_out = (float*)s->acc;
+            p.acc_b = b[st];
+            p.ck = anext[st];
+        } else {
+            p.kin[0] = (const float*)s->acc;
+            p.kc[0] = 1.0;
+            p.nk = 1;
+            p.ck = b[3];
+            p.renorm = 1;
+        }
+        stage_prepare(p);
+        if (!fused_stage(s->d, (float2*)s->S1, p, s->st, &s->timer))
+            return fail(MM_ECUDA, "fused stage kernel could not be launched for this grid");
+        MM_LAUNCHED();
+    }
+    s->s1_fresh = true;
+    s->fsal = false;
+    *used = true;
+    return MM_OK;
+}
+
 template <typename T> mm_status rk4_impl(mm_state* s, double dt, double t) {
+    if constexpr (sizeof(T) == 4) {
+        if (s->use_fused) {
+            bool used = false;
+            MM_TRY(rk4_fused(s, dt, t, &used));
+            if (used) return MM_OK;
+        }
+    }
     const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
     const double anext[3] = {0.5, 0.5, 1.0};
     void* in[4] = {s->m, s->mA, s->mB, s->mA};
@@ -576,6 +630,7 @@ mm_status mm_set_material(mm_state* s, const mm_material* mat, int ptrs_on_devic
     }
     s->have_mat = true;
     s->fsal = false;
+    s->s1_fresh = false;
     return MM_OK;
 }
 
@@ -587,6 +642,7 @@ mm_status mm_set_m(mm_state* s, const void* m, int on_device) {
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
     s->have_m = true;
     s->fsal = false;
+    s->s1_fresh = false;
     return MM_OK;
 }
 
