@@ -543,7 +543,9 @@ p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
 // on timeout the CTA records kErrTmaTimeout, waits (bounded) for its other
 // copy in flight and leaves.
 template <typename T, int L, int B, int DIR>
-__global__ void __launch_bounds__(B * Fft<T, L, DIR, (DIR < 0 && L > 1)>::TPL, 1)
+__global__ void __launch_bounds__(B * Fft<T, L, DIR, (DIR < 0 && L > 1)>::TPL,
+                                  (768 / (B * Fft<T, L, DIR, (DIR < 0 && L > 1)>::TPL)) > 1
+                                      ? 768 / (B * Fft<T, L, DIR, (DIR < 0 && L > 1)>::TPL) : 1)
 p_y_tma(DemagDims d, const __grid_constant__ CUtensorMap in_map, typename Cplx<T>::type* __restrict__ out,
         int box_rows, int nboxes) {
     using C = typename Cplx<T>::type;
@@ -812,7 +814,9 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
 // and its tensor slice (box 16 x 1 x (Pz/2+1) x 6); the S2 part doubles as
 // the transforms' exchange scratch once the registers are loaded.
 template <int LZ, int B>
-__global__ void __launch_bounds__(B * Fft<float, LZ, -1, (LZ > 1)>::TPL, 2)
+__global__ void __launch_bounds__(B * Fft<float, LZ, -1, (LZ > 1)>::TPL,
+                                  (256 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL)) > 1
+                                      ? 256 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL) : 1)
 p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_constant__ CUtensorMap t_map,
          float2* __restrict__ S2, int slot_bytes, int s2_bytes) {
     using C = float2;
@@ -1063,7 +1067,7 @@ template <typename K> static int persistent_grid(K kernel, int threads, size_t s
 
 // TMA y pass (FP32 only): returns false if it could not be used (caller falls back)
 // kx columns per TMA tile: two slots of L x B complex floats stay within 128 KB
-template <int L> constexpr int b_tma() { return (8192 / L) < 16 ? ((8192 / L) < 2 ? 2 : 8192 / L) : 16; }
+template <int L> constexpr int b_tma() { return (4096 / L) < 8 ? ((4096 / L) < 2 ? 2 : 4096 / L) : 8; }
 
 template <int L, int DIR>
 static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cudaStream_t st) {
