@@ -1,0 +1,64 @@
+"""Parity at the benchmark's full size and launch configuration: one RK4 step
+of the bulk workload (256x256x64 cells, FP32 fields, the fused TMA path that
+bench.py times) against one RK4 step of the FP64 oracle on the same inputs.
+
+The update m_{n+1} - m_n = dt * sum(b_s k_s) is compared relative to its own
+size: each field evaluation carries <= 1e-5 relative error in FP32, and m is
+stored in FP32 (6e-8 absolute)."""
+import numpy as np
+import pytest
+
+from gpu_util import oracle_problem, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bulk_full_size_rk4_step_fp32():
+    from oracle.llg import rk4_step
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.bulk()
+    s = setup_workload(w, "fp32")
+    m0_gpu = from_soa(to_host(s.get_m()))
+    s.step(w.dt, 0.0, "rk4")
+    mg = from_soa(to_host(s.get_m()))
+    s.close()
+    prob = oracle_problem(w)
+    mr = rk4_step(prob, w.m0, 0.0, w.dt)
+    inc = np.max(np.abs(mr - w.m0))
+    err = np.max(np.abs(mg - mr))
+    assert inc > 1e-4                      # the step does move m
+    assert err < 2e-5 * inc + 2e-7, (err, inc)
+    assert np.max(np.abs(np.linalg.norm(mg, axis=-1) - 1.0)) < 1e-6
+    # the GPU's own FP32 copy of m0 differs from the FP64 input by rounding only
+    assert np.max(np.abs(m0_gpu - w.m0)) < 1e-7
+
+
+def test_thin_film_dp45_fp32_replayed_by_oracle():
+    """FP32 Dormand-Prince steps on the thin-film workload; the oracle replays
+    the step sizes the GPU accepted (the error norm itself is FP64 on both
+    sides but its inputs differ by FP32 rounding, so the accept decisions are
+    compared only where err is not within 1e-3 of the threshold)."""
+    from oracle.llg import dp45_attempt, normalize
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.thin_film(n=(128, 32, 1))
+    s = setup_workload(w, "fp32")
+    prob = oracle_problem(w)
+    m = w.m0.copy()
+    t, dt = 0.0, 1e-13
+    k1 = prob.rhs(m, t)
+    for _ in range(10):
+        t_new, dt = s.step(dt, t, "dp45", w.extra["rtol"])
+        used = t_new - t
+        y5, k7, _, err = dp45_attempt(prob, m, t, used, k1, w.extra["rtol"])
+        assert err <= 1.0 + 1e-3
+        m = normalize(y5)
+        k1 = k7
+        t = t_new
+    mg = from_soa(to_host(s.get_m()))
+    inc = np.max(np.abs(m - w.m0))
+    assert np.max(np.abs(mg - m)) < 1e-4 * inc + 1e-6
+    s.close()
