@@ -161,6 +161,20 @@ mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rt
 mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* dt_inout,
                    double* t_inout, int* steps_out, double* torque_out);
 
+/* Discrete adjoint of one RK4 step of mm_llg_step (Eq. llg, Sec. 3; the
+ * gradient Sec. 5.2 obtains with autograd), written by hand.  For the step
+ * m_{n+1} = Phi(m_n) of size dt from time t with the state's material, field
+ * and demag settings (renormalisation included):
+ *   lambda_n       = (dPhi/dm_n)^T lambda_np1
+ *   grad_Ms_accum += (dPhi/dMs)^T lambda_np1   (per cell; NULL to skip)
+ * The demag part uses that the convolution is its own transpose.  All four
+ * arrays are device memory in the state's layout and real type (grad_Ms_accum
+ * has nx*ny*nz values); lambda_n must not alias the inputs.  The step's stage
+ * inputs and fields are recomputed from m_n (no forward state is kept).
+ * Enqueues only. */
+mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_np1, void* lambda_n,
+                              void* grad_Ms_accum, double dt, double t);
+
 /* Host-only helper (no GPU): the real-space demag tensor this library builds
  * (Sec. 4.4, same rule as mm_demag_setup) for every cell offset, as
  * 6 x (2nx-1) x (2ny-1) x (2nz-1) doubles, components (xx, xy, xz, yy, yz, zz),

@@ -48,8 +48,10 @@ def rhs_vjp(prob, m, t, u):
     hex_ = exchange_field(m, prob.Ms, prob.A, prob.dx)
     hu = anisotropy_field(m, prob.Ms, prob.Ku1, prob.ku_axis)
     a = alpha[..., None]
+    ok = Ms != 0
+    # a cell with Ms = 0 has f = 0 identically: its cotangent reaches nothing
     v = u + a * np.cross(u, m)
-    w = np.cross(v, m)
+    w = np.cross(v, m) * ok[..., None]
     G = np.cross(m, h)
     inv = np.zeros(prob.n)
     np.divide(1.0, Ms, out=inv, where=Ms != 0)
@@ -60,7 +62,6 @@ def rhs_vjp(prob, m, t, u):
     lam = -gp[..., None] * (np.cross(h, v) + a * np.cross(G, u) + HTw)
     dMs = np.sum(m * hw, axis=-1) - np.sum(w * (hex_ + hu), axis=-1) * inv
     gMs = -gp * dMs
-    ok = Ms != 0
     lam = lam * ok[..., None]
     gMs = gMs * ok
     return lam, gMs

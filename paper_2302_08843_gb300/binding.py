@@ -24,7 +24,7 @@ MM_RK4, MM_DP45 = 0, 1
 EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m", "mm_get_m",
            "mm_set_zeeman", "mm_demag_setup", "mm_demag_disable", "mm_heff", "mm_llg_step",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
-           "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc")
+           "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint")
 
 
 class MMError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
         "mm_last_error": (ctypes.c_char_p, []),
         "mm_version": (ctypes.c_char_p, []),
         "mm_demag_noalloc": (i, [ctypes.POINTER(mm_grid), i, vp, vp, d, vp, vp, vp]),
+        "mm_llg_step_adjoint": (i, [vp, vp, vp, vp, vp, d, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -291,6 +292,16 @@ class State:
         if not (allow_unconverged and st == MM_ENOTCONVERGED):
             check(st)
         return steps.value, tq.value, tc.value, dtc.value
+
+    def step_adjoint(self, m_n, lam_next, dt, t=0.0, grad_Ms=None):
+        """mm_llg_step_adjoint: returns lambda_n; adds (dPhi/dMs)^T lam_next into grad_Ms if given."""
+        import torch
+        m_n = self._as_field(m_n)
+        lam_next = self._as_field(lam_next)
+        lam = torch.empty_like(lam_next)
+        check(lib().mm_llg_step_adjoint(self.h, m_n.data_ptr(), lam_next.data_ptr(), lam.data_ptr(),
+                                        None if grad_Ms is None else grad_Ms.data_ptr(), float(dt), float(t)))
+        return lam
 
     def info(self):
         out = (ctypes.c_int * 5)()

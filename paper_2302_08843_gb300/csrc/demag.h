@@ -44,6 +44,12 @@ template <typename T>
 void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
                  typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm);
 
+template <typename T> struct AdjParams;
+template <typename T> void launch_adj_prep(const AdjParams<T>& p, cudaStream_t st);
+template <typename T> void launch_adj_finish(const AdjParams<T>& p, cudaStream_t st);
+template <typename T>
+void launch_adj_renorm(const T* y, const T* lam, T* lam_y, T* lam_acc, T* u, double cb, int N, cudaStream_t st);
+
 // number of doubles per block in the reduction partials
 constexpr int kNPart = 8;
 // partial / scalar slots

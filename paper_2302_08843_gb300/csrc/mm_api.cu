@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.h"
 #include "demag.h"
 #include "mm.h"
 #include "tensor_host.h"
@@ -153,6 +154,7 @@ struct mm_state {
     void* S2 = nullptr;      // 3 nz Py KXS complex (Py > 1)
     void* tens = nullptr;    // 6 KZ2 KY2 KXS real
     void* K[7] = {nullptr};  // DP45 stage derivatives
+    void* adj[19] = {nullptr};  // adjoint: 3 stage inputs, 4 fields, 4 derivatives, y, lambda_y, 2 u, w, q, hw, part
     void* Ms_cell = nullptr;
     void* A_cell = nullptr;
     void* Ku_cell = nullptr;
@@ -498,6 +500,85 @@ mm_status dp_attempt(mm_state* s, double t, double dt, double rtol, double* err,
     return MM_OK;
 }
 
+template <typename T>
+mm_status adjoint_impl(mm_state* s, const void* m_n, const void* lam_np1, void* lam_n, void* gMs, double dt,
+                       double t) {
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    for (int q = 0; q < 19; ++q)
+        if (!s->adj[q]) MM_TRY(dev_alloc(&s->adj[q], 3 * s->rsz * (size_t)s->N));
+    T** A = reinterpret_cast<T**>(s->adj);
+    T* const* Am = A;          // stage inputs m_2..m_4
+    T* const* Ah = A + 3;      // fields at the four stage inputs
+    T* const* Ak = A + 7;      // stage derivatives
+    T* Ay = A[11];
+    T* Aly = A[12];
+    T* Au[2] = {A[13], A[14]};
+    T* Aw = A[15];
+    T* Aq = A[16];
+    T* Ahw = A[17];
+    T* Apart = A[18];
+    const T* ms[4] = {(const T*)m_n, Am[0], Am[1], Am[2]};
+    // forward recompute of the stage inputs, fields and derivatives
+    for (int st = 0; st < 4; ++st) {
+        MM_TRY(run_demag<T>(s, ms[st]));
+        StageParams<T> p;
+        fill_common<T>(s, p, ms[st], t + kRK4_C[st] * dt);
+        p.mn = (const T*)m_n;
+        p.h_out = Ah[st];
+        p.k_out = Ak[st];
+        p.dt = dt;
+        if (st < 3) {
+            p.next = Am[st];
+            p.ck = kRK4_C[st + 1];
+        }
+        MM_TRY(run_stage<T>(s, p, false));
+    }
+    const T* kin[4] = {Ak[0], Ak[1], Ak[2], Ak[3]};
+    launch_combine<T>((const T*)m_n, kin, b, 4, dt, Ay, s->N, s->st);
+    MM_LAUNCHED();
+    launch_adj_renorm<T>(Ay, (const T*)lam_np1, Aly, (T*)lam_n, Au[0], dt * b[3], (int)s->N, s->st);
+    MM_LAUNCHED();
+    int cur = 0;
+    for (int st = 3; st >= 0; --st) {
+        AdjParams<T> p;
+        std::memset(&p, 0, sizeof(p));
+        p.nx = s->g.nx; p.ny = s->g.ny; p.nz = s->g.nz; p.N = (int)s->N;
+        p.idx2 = (T)(1.0 / (s->g.dx * s->g.dx));
+        p.idy2 = (T)(1.0 / (s->g.dy * s->g.dy));
+        p.idz2 = (T)(1.0 / (s->g.dz * s->g.dz));
+        p.Ms_cell = (const T*)s->Ms_cell; p.Ms = (T)s->Ms;
+        p.A_cell = (const T*)s->A_cell; p.A = (T)s->A;
+        p.Ku_cell = (const T*)s->Ku_cell; p.Ku = (T)s->Ku;
+        p.alpha_cell = (const T*)s->alpha_cell; p.alpha = (T)s->alpha;
+        p.grain = s->grain; p.axis_tab = (const T*)s->axis_tab;
+        p.ex = (T)s->axis[0]; p.ey = (T)s->axis[1]; p.ez = (T)s->axis[2];
+        p.m = ms[st];
+        p.h = Ah[st];
+        p.u = Au[cur];
+        p.w = Aw; p.q = Aq; p.part = Apart;
+        p.hw = s->demag_off ? nullptr : Ahw;
+        p.lam_acc = (T*)lam_n;
+        p.gMs = (T*)gMs;
+        p.u_prev = st > 0 ? Au[1 - cur] : nullptr;
+        p.lam_y = Aly;
+        p.cb = st > 0 ? (T)(dt * b[st - 1]) : (T)0;
+        p.cc = (T)(dt * kRK4_C[st]);
+        launch_adj_prep<T>(p, s->st);
+        MM_LAUNCHED();
+        if (!s->demag_off) {
+            // transpose of the demag map applied to w: the same convolution with Ms = 1
+            s->s1_fresh = false;
+            demag_apply<T>(s->d, Aw, nullptr, (T)1, (typename Cplx<T>::type*)s->S1,
+                           (typename Cplx<T>::type*)s->S2, (const T*)s->tens, Ahw, s->st, &s->timer);
+            MM_LAUNCHED();
+        }
+        launch_adj_finish<T>(p, s->st);
+        MM_LAUNCHED();
+        cur = 1 - cur;
+    }
+    return MM_OK;
+}
+
 double dp_factor(double err) {
     if (err == 0.0) return 5.0;
     return std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
@@ -600,6 +681,7 @@ void mm_state_destroy(mm_state* s) {
                      reinterpret_cast<void**>(&s->dev_err)};
     for (void** b : bufs) dev_free(*b);
     for (int q = 0; q < 7; ++q) dev_free(s->K[q]);
+    for (int q = 0; q < 19; ++q) dev_free(s->adj[q]);
     if (s->h_scalars) cudaFreeHost(s->h_scalars);
     s->timer.destroy();
     delete s;
@@ -754,6 +836,18 @@ mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* 
     if (st != MM_OK) return st;
     if (tq >= tol) return fail(MM_ENOTCONVERGED, "relax: torque %g >= %g after %d steps", tq, tol, steps);
     return MM_OK;
+}
+
+mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_np1, void* lambda_n,
+                              void* grad_Ms_accum, double dt, double t) {
+    MM_TRY(check_state(s));
+    if (!m_n || !lambda_np1 || !lambda_n) return fail(MM_EINVAL, "null m_n, lambda_np1 or lambda_n");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
+    if (lambda_n == lambda_np1 || lambda_n == m_n) return fail(MM_EINVAL, "lambda_n must not alias the inputs");
+    MM_TRY(ready_for_fields(s));
+    MM_TRY(set_device(s));
+    return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)
+                              : adjoint_impl<float>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t);
 }
 
 mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out) {
