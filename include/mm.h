@@ -175,6 +175,51 @@ mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* 
 mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_np1, void* lambda_n,
                               void* grad_Ms_accum, double dt, double t);
 
+/* ---- Batched relaxation (served requests) ----
+ * A batch holds up to `capacity` grids of one shape (nx, ny, nz, cell size),
+ * each a "slot" with its own uniform Ms, A, alpha, magnetisation and
+ * Dormand-Prince step, relaxed as in mm_relax (Sec. 3: integrate with the
+ * material's damping until max |m x h| / Ms < tol).  The demag tensor
+ * spectrum is built once per batch (the size bucket's plan) and shared by
+ * all slots; the stacked grids go through the same FFT passes as one larger
+ * problem, and every slot's arithmetic is private (its own reductions in a
+ * fixed order), so a slot's result does not depend on the other slots.
+ * Device buffers are allocated at creation: mm_batch_footprint gives their
+ * size for admission control.  All work of a batch runs on its stream. */
+typedef struct mm_batch mm_batch;
+
+/* Bytes of device memory mm_batch_create allocates for this shape and capacity. */
+size_t mm_batch_footprint(const mm_grid* grid, mm_precision precision, int capacity);
+
+/* Create a batch (builds the Newell/dipole tensor spectrum with radius p_newell). */
+mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capacity, int p_newell,
+                          void* cuda_stream, mm_batch** out);
+void mm_batch_destroy(mm_batch* b);
+
+/* Load a request into a free slot: uniform material, m0 ([3][nz][ny][nx], the
+ * batch's real type, host or device), first step dt0 (<= 0: 1e-13 s).
+ * MM_EINVAL if the slot is out of range or busy. */
+mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double alpha, const void* m0,
+                            int on_device, double dt0);
+
+/* Free a slot (any state). */
+mm_status mm_batch_clear_slot(mm_batch* b, int slot);
+
+/* Enqueue one DP45 attempt for every running slot (and the first-stage
+ * evaluation of newly loaded slots); asynchronous. */
+mm_status mm_batch_begin(mm_batch* b, double rtol);
+
+/* Wait for the attempt enqueued by mm_batch_begin, accept or reject it per
+ * slot (same rule as mm_llg_step's DP45), and enqueue the accepted updates.
+ * A slot whose torque falls below tol becomes 2 (converged); 3 = max_steps
+ * accepted steps reached; 4 = failed (non-finite values or step underflow).
+ * status/steps/torque: host arrays of `capacity` entries or NULL; status 0 is
+ * an empty slot, 1 a running one. */
+mm_status mm_batch_end(mm_batch* b, double tol, int max_steps, int* status, int* steps, double* torque);
+
+/* Copy a slot's magnetisation out (host copies synchronise). */
+mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
+
 /* Host-only helper (no GPU): the real-space demag tensor this library builds
  * (Sec. 4.4, same rule as mm_demag_setup) for every cell offset, as
  * 6 x (2nx-1) x (2ny-1) x (2nz-1) doubles, components (xx, xy, xz, yy, yz, zz),

@@ -24,7 +24,9 @@ MM_RK4, MM_DP45 = 0, 1
 EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m", "mm_get_m",
            "mm_set_zeeman", "mm_demag_setup", "mm_demag_disable", "mm_heff", "mm_llg_step",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
-           "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint")
+           "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
+           "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
+           "mm_batch_begin", "mm_batch_end", "mm_batch_get_m")
 
 
 class MMError(RuntimeError):
@@ -84,6 +86,14 @@ def lib():
         "mm_version": (ctypes.c_char_p, []),
         "mm_demag_noalloc": (i, [ctypes.POINTER(mm_grid), i, vp, vp, d, vp, vp, vp]),
         "mm_llg_step_adjoint": (i, [vp, vp, vp, vp, vp, d, d]),
+        "mm_batch_footprint": (ctypes.c_size_t, [ctypes.POINTER(mm_grid), i, i]),
+        "mm_batch_create": (i, [ctypes.POINTER(mm_grid), i, i, i, vp, ctypes.POINTER(vp)]),
+        "mm_batch_destroy": (None, [vp]),
+        "mm_batch_set_slot": (i, [vp, i, d, d, d, vp, i, d]),
+        "mm_batch_clear_slot": (i, [vp, i]),
+        "mm_batch_begin": (i, [vp, d]),
+        "mm_batch_end": (i, [vp, d, i, vp, vp, vp]),
+        "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -321,6 +331,71 @@ class State:
         if k < 0:
             raise MMError(MM_ECUDA, "mm_profile_read failed")
         return {names[q].decode(): (counts[q], ms[q]) for q in range(min(k, n))}
+
+
+class Batch:
+    """mm_batch: up to `capacity` same-shape grids relaxed together (one DP45
+    attempt for all running slots per begin/end pair)."""
+
+    def __init__(self, n, dx, precision="fp32", capacity=8, p=20, stream=None):
+        import torch
+        self.n = tuple(int(v) for v in n)
+        self.dx = tuple(float(v) for v in dx)
+        self.prec = MM_FP64 if precision == "fp64" else MM_FP32_FIELDS
+        self.dtype = torch.float64 if self.prec == MM_FP64 else torch.float32
+        self.npdtype = np.float64 if self.prec == MM_FP64 else np.float32
+        self.capacity = int(capacity)
+        self.shape = (3, self.n[2], self.n[1], self.n[0])
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        g = mm_grid(self.n[0], self.n[1], self.n[2], *self.dx)
+        h = ctypes.c_void_p()
+        check(lib().mm_batch_create(ctypes.byref(g), self.prec, self.capacity, int(p),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.footprint = Batch.footprint_of(self.n, self.dx, precision, capacity)
+        self._status = np.zeros(self.capacity, dtype=np.int32)
+        self._steps = np.zeros(self.capacity, dtype=np.int32)
+        self._torque = np.zeros(self.capacity, dtype=np.float64)
+
+    @staticmethod
+    def footprint_of(n, dx, precision, capacity):
+        g = mm_grid(int(n[0]), int(n[1]), int(n[2]), float(dx[0]), float(dx[1]), float(dx[2]))
+        return int(lib().mm_batch_footprint(ctypes.byref(g), MM_FP64 if precision == "fp64" else MM_FP32_FIELDS,
+                                            int(capacity)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_slot(self, slot, Ms, A, alpha, m0, dt0=1e-13):
+        """m0: (3, nz, ny, nx) numpy array (host) or CUDA tensor of the batch's dtype."""
+        if isinstance(m0, np.ndarray):
+            m0 = np.ascontiguousarray(m0, dtype=self.npdtype)
+        p, dev = _ptr(m0)
+        check(lib().mm_batch_set_slot(self.h, int(slot), float(Ms), float(A), float(alpha), p, dev, float(dt0)))
+
+    def clear_slot(self, slot):
+        check(lib().mm_batch_clear_slot(self.h, int(slot)))
+
+    def begin(self, rtol=1e-5):
+        check(lib().mm_batch_begin(self.h, float(rtol)))
+
+    def end(self, tol=1e-3, max_steps=20000):
+        check(lib().mm_batch_end(self.h, float(tol), int(max_steps), self._status.ctypes.data,
+                                 self._steps.ctypes.data, self._torque.ctypes.data))
+        return self._status.copy(), self._steps.copy(), self._torque.copy()
+
+    def get_m(self, slot):
+        out = np.empty(self.shape, dtype=self.npdtype)
+        check(lib().mm_batch_get_m(self.h, int(slot), out.ctypes.data, 0))
+        return out
 
 
 def setup_workload(w, precision="fp64", p=20, stream=None):

@@ -1,0 +1,175 @@
+// Kernels of the batched (served) relax path: nb grids of one shape stacked as
+// a leading batch dimension ([b][3][nz][ny][nx]), each with its own uniform
+// Ms, A, alpha and its own Dormand-Prince step size.  A request's arithmetic
+// never mixes with another's (per-grid reductions in a fixed order), so its
+// result does not depend on which other requests share the batch.
+#include "batch.h"
+
+namespace mm {
+
+__device__ __forceinline__ double bwarp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// one thread per cell, grid (ceil(N/256), nb); a masked-off grid does nothing
+template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(BatchStageParams<T> p) {
+    const int b = blockIdx.y;
+    if (!p.mask[b]) return;                       // uniform per block
+    const int N = p.N;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    const long off = (long)b * 3 * N;
+    double tq = 0.0, er = 0.0, nf = 0.0;
+    if (i < N) {
+        const int x = i % p.nx, yz = i / p.nx, y = yz % p.ny, z = yz / p.ny;
+        const T* m = p.m + off;
+        const T mx = m[i], my = m[N + i], mz = m[2 * N + i];
+        const T Ms = p.Ms[b], A = p.A[b], al = p.alpha[b];
+        T hx = 0, hy = 0, hz = 0, cx = 0, cy = 0, cz = 0;
+        if (Ms != (T)0) {
+            T sx = 0, sy = 0, sz = 0;
+#define MM_BLINK(COND, OFF, ID2)                                              \
+            if (COND) {                                                       \
+                const int k = i + (OFF);                                      \
+                const T w = A * (ID2);                                        \
+                sx += w * (m[k] - mx); sy += w * (m[N + k] - my); sz += w * (m[2 * N + k] - mz); \
+            }
+            MM_BLINK(x > 0, -1, p.idx2)
+            MM_BLINK(x < p.nx - 1, 1, p.idx2)
+            MM_BLINK(y > 0, -p.nx, p.idy2)
+            MM_BLINK(y < p.ny - 1, p.nx, p.idy2)
+            MM_BLINK(z > 0, -p.nx * p.ny, p.idz2)
+            MM_BLINK(z < p.nz - 1, p.nx * p.ny, p.idz2)
+#undef MM_BLINK
+            const T cex = (T)(2.0 / kMu0) / Ms;
+            const T* hd = p.hd + off;
+            hx = hd[i] + cex * sx + (T)p.hx0;
+            hy = hd[N + i] + cex * sy + (T)p.hy0;
+            hz = hd[2 * N + i] + cex * sz + (T)p.hz0;
+        }
+        const T gp = (T)(-kGamma) / ((T)1 + al * al);
+        cx = my * hz - mz * hy; cy = mz * hx - mx * hz; cz = mx * hy - my * hx;
+        const T dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
+        const T kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
+        if (!(isfinite(kx) && isfinite(ky) && isfinite(kz))) nf = 1.0;
+        if (p.want_torque && Ms != (T)0) tq = sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms;
+        if (p.k_out) { T* ko = p.k_out + off; ko[i] = kx; ko[N + i] = ky; ko[2 * N + i] = kz; }
+        if (p.next || p.want_err) {
+            const double dt = p.dt[b];
+            T sxn = (T)p.ck * kx, syn = (T)p.ck * ky, szn = (T)p.ck * kz;
+            double ex_ = p.eb_k * kx, ey_ = p.eb_k * ky, ez_ = p.eb_k * kz;
+            for (int q = 0; q < p.nk; ++q) {
+                const T* kq = p.kin[q] + off;
+                const T ax = kq[i], ay = kq[N + i], az = kq[2 * N + i];
+                sxn += (T)p.kc[q] * ax; syn += (T)p.kc[q] * ay; szn += (T)p.kc[q] * az;
+                if (p.want_err) { ex_ += p.eb[q] * ax; ey_ += p.eb[q] * ay; ez_ += p.eb[q] * az; }
+            }
+            const T* mn = p.mn + off;
+            const T m0x = mn[i], m0y = mn[N + i], m0z = mn[2 * N + i];
+            if (p.want_err) {
+                const double scx = p.rtol + p.rtol * fmax(fabs((double)m0x), fabs((double)mx));
+                const double scy = p.rtol + p.rtol * fmax(fabs((double)m0y), fabs((double)my));
+                const double scz = p.rtol + p.rtol * fmax(fabs((double)m0z), fabs((double)mz));
+                er = fmax(fmax(fabs(dt * ex_) / scx, fabs(dt * ey_) / scy), fabs(dt * ez_) / scz);
+                if (!isfinite(er)) nf = 1.0;
+            }
+            if (p.next) {
+                T* nx_ = p.next + off;
+                nx_[i] = m0x + (T)dt * sxn; nx_[N + i] = m0y + (T)dt * syn; nx_[2 * N + i] = m0z + (T)dt * szn;
+            }
+        }
+    }
+    if (p.partials) {
+        __shared__ double red[8][3];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        tq = bwarp_max(tq); er = bwarp_max(er); nf = bwarp_max(nf);
+        if (lane == 0) { red[wid][0] = tq; red[wid][1] = er; red[wid][2] = nf; }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double a = red[0][threadIdx.x];
+            for (int w = 1; w < 8; ++w) a = fmax(a, red[w][threadIdx.x]);
+            p.partials[((long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = a;
+        }
+    }
+}
+
+// per-grid maxima of the block partials: scalars[b][0..2] = (torque, err, nonfinite)
+__global__ void batch_finalize_kernel(const double* __restrict__ partials, int nblk, double* __restrict__ scalars) {
+    const int b = blockIdx.x;
+    __shared__ double sm[3][128];
+    for (int q = 0; q < 3; ++q) {
+        double a = 0.0;
+        for (int k = threadIdx.x; k < nblk; k += 128) a = fmax(a, partials[((long)b * nblk + k) * 3 + q]);
+        sm[q][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int q = 0; q < 3; ++q) sm[q][threadIdx.x] = fmax(sm[q][threadIdx.x], sm[q][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) scalars[b * 3 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// out[b] = m[b] + dt[b] a k[b] for masked grids
+template <typename T> __global__ void batch_combine_kernel(const T* __restrict__ m, const T* __restrict__ k,
+                                                           const double* __restrict__ dt, double a,
+                                                           const int* __restrict__ mask, T* __restrict__ out, int n3) {
+    const int b = blockIdx.y;
+    if (!mask[b]) return;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n3) return;
+    const long o = (long)b * n3 + i;
+    out[o] = m[o] + (T)(dt[b] * a) * k[o];
+}
+
+// accepted grids: m[b] = y5[b] / |y5[b]|, k1[b] = k7[b]
+template <typename T> __global__ void batch_accept_kernel(const T* __restrict__ y5, const T* __restrict__ k7,
+                                                          const int* __restrict__ acc, T* __restrict__ m,
+                                                          T* __restrict__ k1, int N) {
+    const int b = blockIdx.y;
+    if (!acc[b]) return;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= N) return;
+    const long o = (long)b * 3 * N;
+    T a = y5[o + i], c = y5[o + N + i], e = y5[o + 2 * N + i];
+    const T n2 = a * a + c * c + e * e;
+    if (n2 > (T)0) {
+        const T s = (T)1 / sqrt(n2);
+        a *= s; c *= s; e *= s;
+    }
+    m[o + i] = a; m[o + N + i] = c; m[o + 2 * N + i] = e;
+    k1[o + i] = k7[o + i]; k1[o + N + i] = k7[o + N + i]; k1[o + 2 * N + i] = k7[o + 2 * N + i];
+}
+
+template <typename T> void launch_batch_stage(const BatchStageParams<T>& p, cudaStream_t st) {
+    dim3 grid((p.N + 255) / 256, p.nb);
+    batch_stage_kernel<T><<<grid, 256, 0, st>>>(p);
+}
+void launch_batch_finalize(const double* partials, int nblk, int nb, double* scalars, cudaStream_t st) {
+    batch_finalize_kernel<<<nb, 128, 0, st>>>(partials, nblk, scalars);
+}
+template <typename T> void launch_batch_combine(const T* m, const T* k, const double* dt, double a, const int* mask,
+                                                T* out, int N, int nb, cudaStream_t st) {
+    dim3 grid((3 * N + 255) / 256, nb);
+    batch_combine_kernel<T><<<grid, 256, 0, st>>>(m, k, dt, a, mask, out, 3 * N);
+}
+template <typename T> void launch_batch_accept(const T* y5, const T* k7, const int* acc, T* m, T* k1, int N, int nb,
+                                               cudaStream_t st) {
+    dim3 grid((N + 255) / 256, nb);
+    batch_accept_kernel<T><<<grid, 256, 0, st>>>(y5, k7, acc, m, k1, N);
+}
+
+template void launch_batch_stage<float>(const BatchStageParams<float>&, cudaStream_t);
+template void launch_batch_stage<double>(const BatchStageParams<double>&, cudaStream_t);
+template void launch_batch_combine<float>(const float*, const float*, const double*, double, const int*, float*, int,
+                                          int, cudaStream_t);
+template void launch_batch_combine<double>(const double*, const double*, const double*, double, const int*, double*,
+                                           int, int, cudaStream_t);
+template void launch_batch_accept<float>(const float*, const float*, const int*, float*, float*, int, int,
+                                         cudaStream_t);
+template void launch_batch_accept<double>(const double*, const double*, const int*, double*, double*, int, int,
+                                          cudaStream_t);
+
+}  // namespace mm

@@ -1,0 +1,40 @@
+// Batched (served) relax path: parameters and launchers of csrc/batch.cu.
+#pragma once
+
+#include "demag.h"
+
+namespace mm {
+
+template <typename T> struct BatchStageParams {
+    int nx, ny, nz, N, nb;
+    T idx2, idy2, idz2;
+    const T* Ms;              // [nb] per-grid material (device)
+    const T* A;
+    const T* alpha;
+    const double* dt;         // [nb] per-grid step
+    const int* mask;          // [nb] grids this launch works on
+    double hx0, hy0, hz0;     // uniform external field
+    const T* m;               // stage input [nb][3][N]
+    const T* hd;              // demag field [nb][3][N]
+    const T* mn;              // m at the start of the step
+    T* k_out;
+    T* next;                  // mn + dt (sum_j kc_j kin_j + ck k)
+    const T* kin[7];
+    double kc[7];
+    int nk;
+    double ck;
+    int want_err, want_torque;
+    double eb[7];
+    double eb_k;
+    double rtol;              // atol = rtol
+    double* partials;         // [nb][blocks per grid][3]
+};
+
+template <typename T> void launch_batch_stage(const BatchStageParams<T>& p, cudaStream_t st);
+void launch_batch_finalize(const double* partials, int nblk, int nb, double* scalars, cudaStream_t st);
+template <typename T> void launch_batch_combine(const T* m, const T* k, const double* dt, double a, const int* mask,
+                                                T* out, int N, int nb, cudaStream_t st);
+template <typename T> void launch_batch_accept(const T* y5, const T* k7, const int* acc, T* m, T* k1, int N, int nb,
+                                               cudaStream_t st);
+
+}  // namespace mm

@@ -17,6 +17,8 @@ struct DemagDims {
     int KX;              // LX/2 + 1 spectrum columns
     int KXS;             // row stride of S1/S2 and of the tensor spectrum (elements)
     int* err = nullptr;  // device error word for bounded-wait failures; null: no TMA kernels
+    int nb = 1;          // grids of this shape stacked as a leading batch dimension
+    const void* Ms_b = nullptr;   // per-grid Ms (nb values of the real type) or null
 };
 
 // CUDA-event timing of kernel launches on a stream (inactive unless enabled).

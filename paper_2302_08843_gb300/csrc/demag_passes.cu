@@ -36,6 +36,20 @@ cudaError_t upload_twiddles(const double2* w64, const float2* w32) {
 }
 
 // ------------------------------------------------------------------ P1 ----
+// The x passes transform two real rows per complex FFT.  Rows are paired
+// within one grid of a batch (R = 3 ny nz rows each; an odd R leaves the last
+// row of every grid alone with a zero partner), so that a grid's result never
+// depends on another grid's data.  Line l of block blk is pair q = blk NL + l.
+template <int NL> __device__ __forceinline__ void pair_lines(const DemagDims& d, long* ra_s, long* rb_s) {
+    if (threadIdx.x < NL) {
+        const long R = 3L * d.ny * d.nz, ppg = (R + 1) / 2;
+        const long q = (long)blockIdx.x * NL + threadIdx.x;
+        const long b = q / ppg, lp = q - b * ppg;
+        const bool ok = b < d.nb;
+        ra_s[threadIdx.x] = ok ? b * R + 2 * lp : -1;
+        rb_s[threadIdx.x] = ok && 2 * lp + 1 < R ? b * R + 2 * lp + 1 : -1;
+    }
+}
 template <typename T, int LX, int NL>
 __global__ void __launch_bounds__(NL * Fft<T, LX, -1, (LX > 1)>::TPL)
 p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell, T Ms_const,
@@ -50,20 +64,22 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
     const int tid = threadIdx.x;
     const int line = tid % NL, j = tid / NL;
     const long plane = (long)d.ny * d.nz;
-    const long rows = 3 * plane;
-    const long row0 = (long)blockIdx.x * (2 * NL);
+    const T* Ms_b = static_cast<const T*>(d.Ms_b);
+    __shared__ long ra_s[NL], rb_s[NL];
+    pair_lines<NL>(d, ra_s, rb_s);
+    __syncthreads();
 
     for (int idx = tid; idx < NL * XH; idx += NT) {
         const int l = idx / XH, x = idx - l * XH;
-        const long ra = row0 + 2 * l, rb = ra + 1;
+        const long ra = ra_s[l], rb = rb_s[l];
         T a = 0, b = 0;
         if (x < d.nx) {
-            if (ra < rows) {
-                const T ms = Ms_cell ? Ms_cell[(ra % plane) * d.nx + x] : Ms_const;
+            if (ra >= 0) {
+                const T ms = Ms_b ? Ms_b[ra / (3 * plane)] : (Ms_cell ? Ms_cell[(ra % plane) * d.nx + x] : Ms_const);
                 a = m[ra * d.nx + x] * ms;
             }
-            if (rb < rows) {
-                const T ms = Ms_cell ? Ms_cell[(rb % plane) * d.nx + x] : Ms_const;
+            if (rb >= 0) {
+                const T ms = Ms_b ? Ms_b[rb / (3 * plane)] : (Ms_cell ? Ms_cell[(rb % plane) * d.nx + x] : Ms_const);
                 b = m[rb * d.nx + x] * ms;
             }
         }
@@ -85,11 +101,11 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
     const T half = (T)0.5;
     for (int idx = tid; idx < NL * KXn; idx += NT) {
         const int l = idx / KXn, k = idx - l * KXn;
-        const long ra = row0 + 2 * l, rb = ra + 1;
+        const long ra = ra_s[l], rb = rb_s[l];
         const C zk = s[k * LS + l];
         const C zm = s[((LX - k) & (LX - 1)) * LS + l];
-        if (ra < rows) S1[ra * d.KXS + k] = mk<C>(half * (zk.x + zm.x), half * (zk.y - zm.y));
-        if (rb < rows) S1[rb * d.KXS + k] = mk<C>(half * (zk.y + zm.y), half * (zm.x - zk.x));
+        if (ra >= 0) S1[ra * d.KXS + k] = mk<C>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+        if (rb >= 0) S1[rb * d.KXS + k] = mk<C>(half * (zk.y + zm.y), half * (zm.x - zk.x));
     }
 }
 
@@ -512,7 +528,7 @@ p_y_pass(DemagDims d, const typename Cplx<T>::type* __restrict__ in,
     const int kl = line % B, g = line / B;
     const int kx = blockIdx.x * B + kl;
     const int cz = blockIdx.y * G + g;
-    const bool valid = kx < d.KX && cz < 3 * d.nz;
+    const bool valid = kx < d.KX && cz < d.nb * 3 * d.nz;
     const int rows_in = DIR < 0 ? d.ny : LY;
     const int rows_out = DIR < 0 ? LY : d.ny;
     const C* src = in + ((long)cz * rows_in) * d.KXS + kx;
@@ -656,7 +672,7 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
     const bool valid = kx < d.KX && p < KY2 && (side == 0 || (p > 0 && 2 * p < LY));
     const int ky = side ? LY - p : p;
     const long cstride = (long)d.nz * LY * d.KXS;   // component stride in S2
-    C* col = S2 + (long)ky * d.KXS + kx;            // element (c, z) at col[c*cstride + z*LY*KXS]
+    C* col = S2 + (long)blockIdx.z * 3 * cstride + (long)ky * d.KXS + kx;   // (c, z) at col[c*cstride + z*LY*KXS]
     const long zs = (long)LY * d.KXS;
 
     {   // all loads in flight together, parked at this thread's own (pattern) positions
@@ -751,7 +767,7 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
     const bool valid = kx < d.KX && p < KY2 && (side == 0 || (p > 0 && 2 * p < LY));
     const int ky = side ? LY - p : p;
     const long cstride = (long)d.nz * LY * d.KXS;
-    C* col = S2 + (long)ky * d.KXS + kx;
+    C* col = S2 + (long)blockIdx.z * 3 * cstride + (long)ky * d.KXS + kx;
     const long zs = (long)LY * d.KXS;
 
     C vx[NR], vy[NR], vz[NR];
@@ -942,14 +958,15 @@ p5_x_inverse(DemagDims d, const typename Cplx<T>::type* __restrict__ S1, T* __re
     constexpr int KXn = LX / 2 + 1;
     const int tid = threadIdx.x;
     const int line = tid % NL, j = tid / NL;
-    const long rows = 3L * d.ny * d.nz;
-    const long row0 = (long)blockIdx.x * (2 * NL);
+    __shared__ long ra_s[NL], rb_s[NL];
+    pair_lines<NL>(d, ra_s, rb_s);
+    __syncthreads();
     for (int idx = tid; idx < NL * KXn; idx += NT) {
         const int l = idx / KXn, k = idx - l * KXn;
-        const long ra = row0 + 2 * l, rb = ra + 1;
+        const long ra = ra_s[l], rb = rb_s[l];
         C A = mk<C>(0, 0), Bv = mk<C>(0, 0);
-        if (ra < rows) A = S1[ra * d.KXS + k];
-        if (rb < rows) Bv = S1[rb * d.KXS + k];
+        if (ra >= 0) A = S1[ra * d.KXS + k];
+        if (rb >= 0) Bv = S1[rb * d.KXS + k];
         if (k == 0 || 2 * k == LX) { A.y = 0; Bv.y = 0; }   // a real row has real DC and Nyquist
         s[k * LS + l] = mk<C>(A.x - Bv.y, A.y + Bv.x);
         if (k > 0 && 2 * k < LX) s[(LX - k) * LS + l] = mk<C>(A.x + Bv.y, Bv.x - A.y);
@@ -966,10 +983,10 @@ p5_x_inverse(DemagDims d, const typename Cplx<T>::type* __restrict__ S1, T* __re
     __syncthreads();
     for (int idx = tid; idx < NL * d.nx; idx += NT) {
         const int l = idx / d.nx, x = idx - l * d.nx;
-        const long ra = row0 + 2 * l, rb = ra + 1;
+        const long ra = ra_s[l], rb = rb_s[l];
         const C z = s[x * LS + l];
-        if (ra < rows) h[ra * d.nx + x] = z.x;
-        if (rb < rows) h[rb * d.nx + x] = z.y;
+        if (ra >= 0) h[ra * d.nx + x] = z.x;
+        if (rb >= 0) h[rb * d.nx + x] = z.y;
     }
 }
 
@@ -1001,8 +1018,8 @@ template <typename T, int L> static void launch_p1(const DemagDims& d, const T* 
     constexpr int NL = nl_x<T, L>();
     using C = typename Cplx<T>::type;
     const size_t sm = (size_t)L * (NL + 1) * sizeof(C);
-    const long rows = 3L * d.ny * d.nz;
-    const unsigned grid = (unsigned)((rows + 2 * NL - 1) / (2 * NL));
+    const long pairs = (long)d.nb * ((3L * d.ny * d.nz + 1) / 2);
+    const unsigned grid = (unsigned)((pairs + NL - 1) / NL);
     auto k = p1_x_forward<T, L, NL>;
     set_smem(k, sm);
     k<<<grid, NL * tpl_of<T, L>(), sm, st>>>(d, m, Ms_cell, Ms, S1);
@@ -1013,8 +1030,8 @@ template <typename T, int L> static void launch_p5(const DemagDims& d, const typ
     constexpr int NL = nl_x<T, L>();
     using C = typename Cplx<T>::type;
     const size_t sm = (size_t)L * (NL + 1) * sizeof(C);
-    const long rows = 3L * d.ny * d.nz;
-    const unsigned grid = (unsigned)((rows + 2 * NL - 1) / (2 * NL));
+    const long pairs = (long)d.nb * ((3L * d.ny * d.nz + 1) / 2);
+    const unsigned grid = (unsigned)((pairs + NL - 1) / NL);
     auto k = p5_x_inverse<T, L, NL>;
     set_smem(k, sm);
     k<<<grid, NL * tpl_of<T, L>(), sm, st>>>(d, S1, h);
@@ -1025,7 +1042,7 @@ template <typename T, int L, int DIR> static void launch_py(const DemagDims& d, 
     constexpr int B = b_of<T, L>(), G = g_of<T, L>();
     using C = typename Cplx<T>::type;
     const size_t sm = (size_t)L * B * G * sizeof(C);
-    dim3 grid((d.KX + B - 1) / B, (3 * d.nz + G - 1) / G);
+    dim3 grid((d.KX + B - 1) / B, (d.nb * 3 * d.nz + G - 1) / G);
     auto k = p_y_pass<T, L, B, G, DIR>;
     set_smem(k, sm);
     k<<<grid, B * G * tpl_of<T, L>(), sm, st>>>(d, in, out);
@@ -1074,7 +1091,7 @@ static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cud
     constexpr int B = b_tma<L>();
     using F = Fft<float, L, DIR, (DIR < 0 && L > 1)>;
     const int rows_in = DIR < 0 ? d.ny : L;
-    if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
+    if (!d.err || d.nb != 1 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     const int box_rows = rows_in < 256 ? rows_in : 256;
     const int nboxes = (rows_in + box_rows - 1) / box_rows;
     if ((size_t)nboxes * box_rows > (size_t)L) return false;
@@ -1146,7 +1163,9 @@ static int box_width(int n, int* nboxes) {
 template <int L> static bool launch_p1_tma(const DemagDims& d, const float* m, const float* Ms_cell, float Ms,
                                            float2* S1, cudaStream_t st) {
     constexpr int NL = nl_x<float, L>();
-    if (!d.err || Ms_cell || L < 16 || (d.nx * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(m) & 15) != 0) return false;
+    if (!d.err || d.nb != 1 || d.Ms_b || Ms_cell || L < 16 || (d.nx * 4) % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(m) & 15) != 0)
+        return false;
     if (2 * NL > 256) return false;
     int nb = 0;
     const int w = box_width(d.nx, &nb);
@@ -1176,7 +1195,8 @@ template <int L> static bool launch_p1_tma(const DemagDims& d, const float* m, c
 
 template <int L> static bool launch_p5_tma(const DemagDims& d, const float2* S1, float* h, cudaStream_t st) {
     constexpr int NL = nl_x<float, L>();
-    if (!d.err || L < 16 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
+    if (!d.err || d.nb != 1 || L < 16 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0)
+        return false;
     if (2 * NL > 256) return false;
     int nb = 0;
     const int w = box_width(d.KX, &nb);
@@ -1203,12 +1223,12 @@ template <typename T, int L> static void launch_p3(const DemagDims& d, typename 
     constexpr int B = b_of<T, L>(), G = g_of<T, L>();
     using C = typename Cplx<T>::type;
     const int kyi = 2 * (d.LY / 2 + 1);
-    dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G);
+    dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G, d.nb);
     if constexpr (sizeof(T) == 4 && L <= 256) {
-        if (launch_p3_tma<L>(d, S2, tens, st)) return;
+        if (d.nb == 1 && launch_p3_tma<L>(d, S2, tens, st)) return;
         // 128-thread CTAs: three fit per SM at up to 170 registers per thread
         constexpr int G3 = (B * tpl_of<T, L>() >= 128) ? 1 : 128 / (B * tpl_of<T, L>());
-        dim3 grid3((d.KX + B - 1) / B, (kyi + G3 - 1) / G3);
+        dim3 grid3((d.KX + B - 1) / B, (kyi + G3 - 1) / G3, d.nb);
         const size_t sm = (size_t)L * B * G3 * sizeof(C);
         auto k = p3_z_conv_reg<T, L, B, G3>;
         set_smem(k, sm);

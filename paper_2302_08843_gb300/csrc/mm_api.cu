@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "adjoint.h"
+#include "batch.h"
 #include "demag.h"
 #include "mm.h"
 #include "tensor_host.h"
@@ -611,6 +612,201 @@ mm_status dp_step(mm_state* s, double* dt_inout, double rtol, double* t_inout, d
 
 }  // namespace
 
+// ================================================================ batch ====
+struct mm_batch {
+    mm_grid g{};
+    mm_precision prec = MM_FP32_FIELDS;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int cap = 0;
+    long N = 0;
+    size_t rsz = 4, csz = 8;
+    DemagDims d{};
+    void* m = nullptr;
+    void* K[7] = {nullptr};
+    void* Y[2] = {nullptr};
+    void* hd = nullptr;
+    void* S1 = nullptr;
+    void* S2 = nullptr;
+    void* tens = nullptr;
+    void* Ms_d = nullptr;
+    void* A_d = nullptr;
+    void* alpha_d = nullptr;
+    double* dt_d = nullptr;
+    int* mask_d = nullptr;       // [2][cap]: first-stage mask, attempt mask
+    int* acc_d = nullptr;
+    double* partials = nullptr;
+    int nblk = 0;
+    double* scal_d = nullptr;    // [2][cap][3]: first stage, attempt
+    double* scal_h = nullptr;    // pinned mirror
+    int* mask_h = nullptr;       // pinned [2][cap]
+    int* acc_h = nullptr;        // pinned [cap]
+    double* dt_h = nullptr;      // pinned [cap]
+    int y5 = 0;                  // which Y buffer holds the last attempt's fifth-order solution
+    int nact = 0;                // slots [0, nact) are launched (highest running slot + 1)
+    double rtol = 1e-5;
+    bool pending = false;
+    std::vector<int> status, steps;
+    std::vector<double> t, dt, torque, Ms, A, alpha;
+    std::vector<char> fresh;     // first stage not evaluated yet
+};
+
+namespace {
+
+size_t batch_bytes(const mm_grid* g, mm_precision prec, int cap, int* LXo, int* LYo, int* LZo, int* KXSo) {
+    const int LX = g->nx == 1 ? 1 : next_pow2(2 * g->nx);
+    const int LY = g->ny == 1 ? 1 : next_pow2(2 * g->ny);
+    const int LZ = g->nz == 1 ? 1 : next_pow2(2 * g->nz);
+    const size_t rsz = prec == MM_FP64 ? 8 : 4, csz = 2 * rsz;
+    const int align = (int)(128 / csz);
+    const int KX = LX / 2 + 1, KXS = (KX + align - 1) / align * align;
+    const size_t N = (size_t)g->nx * g->ny * g->nz;
+    size_t bytes = (size_t)cap * 3 * N * rsz * (1 + 7 + 2 + 1);               // m, K, Y, hd
+    bytes += (size_t)cap * 3 * csz * g->ny * g->nz * KXS;                       // S1
+    if (LY > 1) bytes += (size_t)cap * 3 * csz * g->nz * LY * KXS;              // S2
+    bytes += 6 * rsz * (size_t)(LZ / 2 + 1) * (LY / 2 + 1) * KXS;               // tensor
+    const size_t nblk = (N + 255) / 256;
+    bytes += (size_t)cap * (nblk * 3 * 8 + 3 * rsz + 8 + 3 * 4 + 2 * 3 * 8);
+    if (LXo) { *LXo = LX; *LYo = LY; *LZo = LZ; *KXSo = KXS; }
+    return bytes;
+}
+
+template <typename T> mm_status batch_stage(mm_batch* b, const void* m, const void* mn, void* k_out, void* next,
+                                            const int* mask, int st, bool err, bool torque, double* partials) {
+    BatchStageParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = b->g.nx; p.ny = b->g.ny; p.nz = b->g.nz; p.N = (int)b->N; p.nb = b->nact;
+    p.idx2 = (T)(1.0 / (b->g.dx * b->g.dx));
+    p.idy2 = (T)(1.0 / (b->g.dy * b->g.dy));
+    p.idz2 = (T)(1.0 / (b->g.dz * b->g.dz));
+    p.Ms = (const T*)b->Ms_d; p.A = (const T*)b->A_d; p.alpha = (const T*)b->alpha_d;
+    p.dt = b->dt_d;
+    p.mask = mask;
+    p.m = (const T*)m; p.hd = (const T*)b->hd; p.mn = (const T*)mn;
+    p.k_out = (T*)k_out; p.next = (T*)next;
+    if (st >= 1 && st <= 6) {
+        if (st < 6) {
+            for (int q = 0; q < st; ++q) { p.kin[q] = (const T*)b->K[q]; p.kc[q] = kDP_A[st + 1][q]; }
+            p.nk = st;
+            p.ck = kDP_A[st + 1][st];
+        } else {
+            for (int q = 0; q < 6; ++q) { p.kin[q] = (const T*)b->K[q]; p.eb[q] = kDP_B5[q] - kDP_B4[q]; }
+            p.nk = 6;
+            p.eb_k = kDP_B5[6] - kDP_B4[6];
+        }
+    }
+    p.want_err = err;
+    p.want_torque = torque;
+    p.partials = partials;
+    p.rtol = b->rtol;
+    launch_batch_stage<T>(p, b->st);
+    MM_LAUNCHED();
+    return MM_OK;
+}
+
+template <typename T> mm_status batch_demag(mm_batch* b, const void* m) {
+    using C = typename Cplx<T>::type;
+    KernelTimer off;
+    demag_apply<T>(b->d, (const T*)m, nullptr, (T)0, (C*)b->S1, (C*)b->S2, (const T*)b->tens, (T*)b->hd, b->st, &off);
+    MM_LAUNCHED();
+    return MM_OK;
+}
+
+template <typename T> mm_status batch_begin_impl(mm_batch* b, double rtol) {
+    const int cap = b->cap;
+    b->rtol = rtol;
+    int nnew = 0, nrun = 0, hi = 0;
+    for (int i = 0; i < cap; ++i) {
+        b->mask_h[i] = (b->status[i] == 1 && b->fresh[i]) ? 1 : 0;
+        b->mask_h[cap + i] = b->status[i] == 1 ? 1 : 0;
+        b->dt_h[i] = b->dt[i];
+        nnew += b->mask_h[i];
+        nrun += b->mask_h[cap + i];
+        if (b->status[i] == 1) hi = i + 1;
+    }
+    b->pending = nrun > 0;
+    if (!nrun) return MM_OK;
+    // grids past the highest running slot are not launched at all; the
+    // masked ones below it cost one early-exiting block per tile
+    b->nact = hi;
+    b->d.nb = hi;
+    MM_CUDA(cudaMemcpyAsync(b->mask_d, b->mask_h, sizeof(int) * 2 * cap, cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->dt_d, b->dt_h, sizeof(double) * cap, cudaMemcpyHostToDevice, b->st));
+    double* p0 = b->partials;
+    double* p1 = b->partials + (size_t)cap * b->nblk * 3;
+    if (nnew) {
+        // k1 = f(m) and the initial torque of newly loaded slots
+        MM_TRY(batch_demag<T>(b, b->m));
+        MM_TRY(batch_stage<T>(b, b->m, b->m, b->K[0], nullptr, b->mask_d, 0, false, true, p0));
+        launch_batch_finalize(p0, b->nblk, hi, b->scal_d, b->st);
+        MM_LAUNCHED();
+    }
+    const int* run = b->mask_d + cap;
+    launch_batch_combine<T>((const T*)b->m, (const T*)b->K[0], b->dt_d, kDP_A[1][0], run, (T*)b->Y[0], (int)b->N,
+                            hi, b->st);
+    MM_LAUNCHED();
+    int cur = 0;
+    for (int st = 1; st <= 6; ++st) {
+        MM_TRY(batch_demag<T>(b, b->Y[cur]));
+        if (st < 6) {
+            MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[st], b->Y[1 - cur], run, st, false, false, nullptr));
+            cur = 1 - cur;
+        } else {
+            MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[6], nullptr, run, 6, true, true, p1));
+            b->y5 = cur;
+        }
+    }
+    launch_batch_finalize(p1, b->nblk, hi, b->scal_d + 3 * cap, b->st);
+    MM_LAUNCHED();
+    MM_CUDA(cudaMemcpyAsync(b->scal_h, b->scal_d, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, b->st));
+    return MM_OK;
+}
+
+template <typename T> mm_status batch_end_impl(mm_batch* b, double tol, int max_steps) {
+    const int cap = b->cap;
+    if (!b->pending) return MM_OK;
+    MM_CUDA(cudaStreamSynchronize(b->st));
+    b->pending = false;
+    int nacc = 0;
+    for (int i = 0; i < cap; ++i) {
+        b->acc_h[i] = 0;
+        if (b->status[i] != 1) continue;
+        if (b->fresh[i]) {
+            b->fresh[i] = 0;
+            const double tq0 = b->scal_h[3 * i + 0];
+            if (b->scal_h[3 * i + 2] != 0.0 || !std::isfinite(tq0)) { b->status[i] = 4; continue; }
+            b->torque[i] = tq0;
+            if (tq0 < tol) { b->status[i] = 2; continue; }     // already relaxed: the attempt is discarded
+        }
+        const double tq = b->scal_h[3 * (cap + i) + 0];
+        const double err = b->scal_h[3 * (cap + i) + 1];
+        if (b->scal_h[3 * (cap + i) + 2] != 0.0 || !std::isfinite(err)) { b->status[i] = 4; continue; }
+        const double f = dp_factor(err);
+        if (err <= 1.0) {
+            b->acc_h[i] = 1;
+            ++nacc;
+            b->t[i] += b->dt[i];
+            b->steps[i] += 1;
+            b->torque[i] = tq;
+            b->dt[i] *= f;
+            if (tq < tol) b->status[i] = 2;
+            else if (b->steps[i] >= max_steps) b->status[i] = 3;
+        } else {
+            b->dt[i] *= f;
+            if (!(b->dt[i] >= 1e-22)) b->status[i] = 4;
+        }
+    }
+    if (nacc) {
+        MM_CUDA(cudaMemcpyAsync(b->acc_d, b->acc_h, sizeof(int) * cap, cudaMemcpyHostToDevice, b->st));
+        launch_batch_accept<T>((const T*)b->Y[b->y5], (const T*)b->K[6], b->acc_d, (T*)b->m, (T*)b->K[0], (int)b->N,
+                               b->nact, b->st);
+        MM_LAUNCHED();
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
 // ================================================================= ABI ====
 extern "C" {
 
@@ -848,6 +1044,187 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)
                               : adjoint_impl<float>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t);
+}
+
+size_t mm_batch_footprint(const mm_grid* grid, mm_precision precision, int capacity) {
+    if (!grid || capacity < 1) return 0;
+    return batch_bytes(grid, precision, capacity, nullptr, nullptr, nullptr, nullptr);
+}
+
+void mm_batch_destroy(mm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->st);
+    void** bufs[] = {&b->m, &b->Y[0], &b->Y[1], &b->hd, &b->S1, &b->S2, &b->tens, &b->Ms_d, &b->A_d, &b->alpha_d,
+                     reinterpret_cast<void**>(&b->dt_d), reinterpret_cast<void**>(&b->mask_d),
+                     reinterpret_cast<void**>(&b->acc_d), reinterpret_cast<void**>(&b->partials),
+                     reinterpret_cast<void**>(&b->scal_d)};
+    for (void** q : bufs) dev_free(*q);
+    for (int q = 0; q < 7; ++q) dev_free(b->K[q]);
+    if (b->scal_h) cudaFreeHost(b->scal_h);
+    if (b->mask_h) cudaFreeHost(b->mask_h);
+    if (b->acc_h) cudaFreeHost(b->acc_h);
+    if (b->dt_h) cudaFreeHost(b->dt_h);
+    delete b;
+}
+
+mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capacity, int p_newell, void* cuda_stream,
+                          mm_batch** out) {
+    if (!grid || !out) return fail(MM_EINVAL, "null argument");
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0))
+        return fail(MM_EINVAL, "bad grid");
+    if (capacity < 1 || capacity > 4096) return fail(MM_EINVAL, "capacity must be in 1..4096");
+    if (precision != MM_FP64 && precision != MM_FP32_FIELDS) return fail(MM_EINVAL, "bad precision");
+    if ((double)grid->nx * grid->ny * grid->nz * capacity * 3 >= 2147483648.0) return fail(MM_EINVAL, "batch too large");
+    int LX, LY, LZ, KXS;
+    batch_bytes(grid, precision, capacity, &LX, &LY, &LZ, &KXS);
+    if (LX > kMaxFft || LY > kMaxFft || LZ > kMaxFft) return fail(MM_EINVAL, "padded FFT extent above %d", kMaxFft);
+    mm_batch* b = new (std::nothrow) mm_batch();
+    if (!b) return fail(MM_ENOMEM, "host allocation");
+    auto bail = [&](mm_status st) { mm_batch_destroy(b); return st; };
+    b->g = *grid;
+    b->prec = precision;
+    b->st = (cudaStream_t)cuda_stream;
+    b->cap = capacity;
+    b->N = (long)grid->nx * grid->ny * grid->nz;
+    b->rsz = precision == MM_FP64 ? 8 : 4;
+    b->csz = 2 * b->rsz;
+    b->d = DemagDims{grid->nx, grid->ny, grid->nz, LX, LY, LZ, LX / 2 + 1, KXS};
+    b->d.nb = capacity;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) return bail(fail(MM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    mm_status st = ensure_twiddles(b->device);
+    if (st != MM_OK) return bail(st);
+    const size_t v3 = (size_t)capacity * 3 * b->rsz * b->N;
+    void** bufs[] = {&b->m, &b->Y[0], &b->Y[1], &b->hd};
+    for (void** q : bufs)
+        if ((st = dev_alloc(q, v3)) != MM_OK) return bail(st);
+    for (int q = 0; q < 7; ++q)
+        if ((st = dev_alloc(&b->K[q], v3)) != MM_OK) return bail(st);
+    const size_t s1 = (size_t)capacity * 3 * b->csz * grid->ny * grid->nz * KXS;
+    const size_t s2 = LY > 1 ? (size_t)capacity * 3 * b->csz * grid->nz * LY * KXS : 0;
+    if ((st = dev_alloc(&b->S1, s1)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->S2, s2)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->Ms_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->A_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->alpha_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->dt_d), sizeof(double) * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->mask_d), sizeof(int) * 2 * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->acc_d), sizeof(int) * capacity)) != MM_OK) return bail(st);
+    b->nblk = (int)((b->N + 255) / 256);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->partials), sizeof(double) * 2 * 3 * (size_t)capacity * b->nblk)) !=
+        MM_OK)
+        return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->scal_d), sizeof(double) * 6 * capacity)) != MM_OK) return bail(st);
+    if (cudaMallocHost(reinterpret_cast<void**>(&b->scal_h), sizeof(double) * 6 * capacity) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->mask_h), sizeof(int) * 2 * capacity) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->acc_h), sizeof(int) * capacity) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->dt_h), sizeof(double) * capacity) != cudaSuccess)
+        return bail(fail(MM_ENOMEM, "cudaMallocHost"));
+    b->d.Ms_b = b->Ms_d;
+    // the size bucket's plan: tensor spectrum of this shape, shared by every slot
+    const int n[3] = {grid->nx, grid->ny, grid->nz};
+    const double dd[3] = {grid->dx, grid->dy, grid->dz};
+    const int P[3] = {LX, LY, LZ};
+    std::vector<double> spec;
+    tensor_spectrum(n, dd, p_newell, P, KXS, spec);
+    if ((st = dev_alloc(&b->tens, b->rsz * spec.size())) != MM_OK) return bail(st);
+    if (precision == MM_FP64) {
+        e = cudaMemcpy(b->tens, spec.data(), sizeof(double) * spec.size(), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> f(spec.size());
+        for (size_t i = 0; i < spec.size(); ++i) f[i] = (float)spec[i];
+        e = cudaMemcpy(b->tens, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->S1, 0, s1, b->st);
+    if (e == cudaSuccess && s2) e = cudaMemsetAsync(b->S2, 0, s2, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->m, 0, v3, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->Ms_d, 0, b->rsz * capacity, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return bail(fail(MM_ECUDA, "batch set-up: %s", cudaGetErrorString(e)));
+    b->status.assign(capacity, 0);
+    b->steps.assign(capacity, 0);
+    b->t.assign(capacity, 0.0);
+    b->dt.assign(capacity, 1e-13);
+    b->torque.assign(capacity, 0.0);
+    b->Ms.assign(capacity, 0.0);
+    b->A.assign(capacity, 0.0);
+    b->alpha.assign(capacity, 0.0);
+    b->fresh.assign(capacity, 0);
+    *out = b;
+    return MM_OK;
+}
+
+mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double alpha, const void* m0, int on_device,
+                            double dt0) {
+    if (!b || !m0) return fail(MM_EINVAL, "null argument");
+    if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    if (b->status[slot] != 0) return fail(MM_EINVAL, "slot %d is busy", slot);
+    if (!(Ms >= 0) || !(A >= 0) || !(alpha >= 0)) return fail(MM_EINVAL, "bad material");
+    MM_CUDA(cudaSetDevice(b->device));
+    const size_t v = 3 * b->rsz * (size_t)b->N;
+    MM_CUDA(cudaMemcpyAsync(static_cast<char*>(b->m) + slot * v, m0, v,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->st));
+    const double mat[3] = {Ms, A, alpha};
+    void* dst[3] = {b->Ms_d, b->A_d, b->alpha_d};
+    for (int q = 0; q < 3; ++q) {
+        if (b->prec == MM_FP64) {
+            MM_CUDA(cudaMemcpyAsync(static_cast<double*>(dst[q]) + slot, &mat[q], 8, cudaMemcpyHostToDevice, b->st));
+        } else {
+            const float f = (float)mat[q];
+            MM_CUDA(cudaMemcpyAsync(static_cast<float*>(dst[q]) + slot, &f, 4, cudaMemcpyHostToDevice, b->st));
+        }
+    }
+    MM_CUDA(cudaStreamSynchronize(b->st));   // the host values above are stack copies
+    b->status[slot] = 1;
+    b->steps[slot] = 0;
+    b->t[slot] = 0.0;
+    b->dt[slot] = dt0 > 0 ? dt0 : 1e-13;
+    b->torque[slot] = 0.0;
+    b->Ms[slot] = Ms; b->A[slot] = A; b->alpha[slot] = alpha;
+    b->fresh[slot] = 1;
+    return MM_OK;
+}
+
+mm_status mm_batch_clear_slot(mm_batch* b, int slot) {
+    if (!b) return fail(MM_EINVAL, "null batch");
+    if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    if (b->pending) return fail(MM_EINVAL, "an attempt is in flight: call mm_batch_end first");
+    b->status[slot] = 0;
+    b->fresh[slot] = 0;
+    return MM_OK;
+}
+
+mm_status mm_batch_begin(mm_batch* b, double rtol) {
+    if (!b) return fail(MM_EINVAL, "null batch");
+    if (!(rtol > 0)) return fail(MM_EINVAL, "rtol must be > 0");
+    if (b->pending) return fail(MM_EINVAL, "an attempt is already in flight");
+    MM_CUDA(cudaSetDevice(b->device));
+    return b->prec == MM_FP64 ? batch_begin_impl<double>(b, rtol) : batch_begin_impl<float>(b, rtol);
+}
+
+mm_status mm_batch_end(mm_batch* b, double tol, int max_steps, int* status, int* steps, double* torque) {
+    if (!b) return fail(MM_EINVAL, "null batch");
+    MM_CUDA(cudaSetDevice(b->device));
+    MM_TRY(b->prec == MM_FP64 ? batch_end_impl<double>(b, tol, max_steps) : batch_end_impl<float>(b, tol, max_steps));
+    for (int i = 0; i < b->cap; ++i) {
+        if (status) status[i] = b->status[i];
+        if (steps) steps[i] = b->steps[i];
+        if (torque) torque[i] = b->torque[i];
+    }
+    return MM_OK;
+}
+
+mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device) {
+    if (!b || !m_out) return fail(MM_EINVAL, "null argument");
+    if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    MM_CUDA(cudaSetDevice(b->device));
+    const size_t v = 3 * b->rsz * (size_t)b->N;
+    MM_CUDA(cudaMemcpyAsync(m_out, static_cast<char*>(b->m) + slot * v, v,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st));
+    if (!on_device) MM_CUDA(cudaStreamSynchronize(b->st));
+    return MM_OK;
 }
 
 mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out) {

@@ -1,0 +1,115 @@
+"""GPU tests of the batched relax path and the continuous-batching server:
+batched FP64 relaxation against the oracle (including a grid with an odd row
+count per grid and a 1-cell grid that is relaxed from the start), FP32
+batched relaxation against the FP64 oracle, and the same result for every
+request alone and in the mix (bitwise: per-grid arithmetic and reductions)."""
+import numpy as np
+import pytest
+
+from gpu_util import FP32_TOL, oracle_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _req(rng, n, name="r", dx=(3e-9, 3e-9, 3e-9)):
+    from paper_2302_08843_gb300.workloads import Workload
+    m0 = rng.normal(size=n + (3,))
+    m0 /= np.linalg.norm(m0, axis=-1, keepdims=True)
+    return Workload(name, n, dx, Ms=float(rng.uniform(6e5, 1.2e6)), A=float(rng.uniform(1e-11, 2e-11)),
+                    alpha=1.0, m0=m0)
+
+
+def _drive(b, tol, max_steps):
+    while True:
+        b.begin(1e-5)
+        st, steps, tq = b.end(tol, max_steps)
+        if not np.any(st == 1):
+            return st, steps, tq
+
+
+@pytest.mark.parametrize("n", [(7, 5, 3), (12, 8, 2)])
+def test_batched_relax_fp64_matches_oracle(n):
+    from oracle.llg import relax
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    rng = np.random.default_rng(21)
+    reqs = [_req(rng, n) for _ in range(3)]
+    b = Batch(n, reqs[0].dx, "fp64", capacity=4)
+    for slot, w in zip((0, 2, 3), reqs):      # slot 1 stays empty
+        b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
+    st, steps, tq = _drive(b, 1e-3, 5000)
+    assert st[1] == 0
+    for slot, w in zip((0, 2, 3), reqs):
+        mr, steps_r, tq_r, _ = relax(oracle_problem(w), w.m0, tol=1e-3, max_steps=5000)
+        assert st[slot] == 2
+        assert steps[slot] == steps_r
+        assert abs(tq[slot] - tq_r) < 1e-6 * tq_r
+        assert rel(from_soa(b.get_m(slot)), mr) < 1e-8
+    b.close()
+
+
+def test_batched_fixed_steps_fp32_vs_fp64_oracle():
+    from oracle.llg import relax
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    rng = np.random.default_rng(22)
+    n = (16, 8, 2)
+    reqs = [_req(rng, n) for _ in range(2)]
+    b = Batch(n, reqs[0].dx, "fp32", capacity=2)
+    for slot, w in enumerate(reqs):
+        b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
+    st, steps, _ = _drive(b, 1e-12, 20)      # unreachable tolerance: 20 accepted steps each
+    for slot, w in enumerate(reqs):
+        mr, steps_r, _, _ = relax(oracle_problem(w), w.m0, tol=1e-12, max_steps=20)
+        assert st[slot] == 3 and steps[slot] == steps_r == 20
+        # per field evaluation the FP32 path is within 1e-5; 20 steps accumulate it
+        assert rel(from_soa(b.get_m(slot)), mr) < 20 * FP32_TOL
+    b.close()
+
+
+def test_relaxed_at_start_converges_without_steps():
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.workloads import to_soa
+    m0 = np.array([[[[0.6, 0.0, 0.8]]]])            # one cube cell: h_demag is parallel to m
+    b = Batch((1, 1, 1), (2e-9, 2e-9, 2e-9), "fp64", capacity=2)
+    b.set_slot(1, 8e5, 1.3e-11, 1.0, to_soa(m0))
+    st, steps, tq = _drive(b, 1e-3, 100)
+    assert st[1] == 2 and steps[1] == 0 and tq[1] < 1e-12
+    assert np.array_equal(b.get_m(1).reshape(3), np.array([0.6, 0.0, 0.8]))
+    b.close()
+
+
+def test_same_alone_and_in_the_mix():
+    """Each request's result (m bitwise, step count, torque) served alone equals
+    the one served in a mix of grid sizes, slots and join times."""
+    from paper_2302_08843_gb300.serving import Server
+    rng = np.random.default_rng(23)
+    grids = [(16, 16, 1), (12, 6, 3), (20, 10, 2)]
+    reqs = [(0.0, _req(rng, grids[i % 3], "r%d" % i)) for i in range(10)]
+    mix = Server(precision="fp32", capacity=3, max_states_per_bucket=1, tol=1e-3, max_steps=3000)
+    res_mix = mix.run(reqs, realtime=False, keep_m=True)
+    mix.close()
+    assert all(r["status"] == 2 for r in res_mix)
+    for (arr, w), rm in zip(reqs, res_mix):
+        alone = Server(precision="fp32", capacity=3, tol=1e-3, max_steps=3000)
+        ra = alone.run([(0.0, w)], realtime=False, keep_m=True)[0]
+        alone.close()
+        assert ra["steps"] == rm["steps"]
+        assert ra["torque"] == rm["torque"]
+        assert np.array_equal(ra["m"], rm["m"])
+
+
+def test_served_stream_small():
+    """A short Poisson stream through the real-time loop: every request
+    converges and latencies are reported."""
+    from paper_2302_08843_gb300.serving import Server, latency_summary
+    rng = np.random.default_rng(24)
+    grids = [(32, 32, 1), (16, 8, 4), (25, 25, 2)]
+    t = np.cumsum(rng.exponential(2e-3, size=16))
+    reqs = [(float(t[i] - t[0]), _req(rng, grids[int(rng.integers(3))])) for i in range(16)]
+    srv = Server(precision="fp32", capacity=4, tol=1e-3, max_steps=20000)
+    res = srv.run(reqs, realtime=True)
+    s = latency_summary(res, srv.elapsed)
+    srv.close()
+    assert s["converged"] == 16
+    assert 0 < s["p50_s"] <= s["p99_s"]
