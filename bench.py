@@ -278,6 +278,66 @@ def e2e_measure(torch, s, w, steps, warmup):
     return el, nbytes
 
 
+def serve_measure(torch, n_requests):
+    """The served stream (Poisson arrivals, mean 2 ms; five grid shapes; FP32
+    batched relax under a 40 GB footprint cap): p50/p99 latency and
+    throughput of its first n_requests requests, next to the plain per-solve
+    path (one mm_relax per request, FP64 and FP32) timed over a bounded number
+    of DP45 steps on one request of every shape, compared in accepted
+    cell-steps/s.  The FP32 field error is measured against the FP64 path on
+    each shape."""
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.serving import Server, latency_summary
+    stream = W.serving_stream()
+    reqs = stream[:n_requests]
+    srv = Server(precision="fp32", hbm_cap=40e9)
+    res = srv.run(reqs, realtime=True)
+    summ = latency_summary(res, srv.elapsed)
+    cell_steps = sum(w.ncells * r["steps"] for (_, w), r in zip(reqs, res))
+    summ.update({"elapsed_s": round(srv.elapsed, 3), "graph_launches": srv.launches,
+                 "cell_steps_per_s": cell_steps / srv.elapsed, "peak_footprint_bytes": int(srv.peak_used),
+                 "sample": "first %d of the 512-request stream (arrivals as drawn)" % len(reqs)})
+    srv.close()
+    torch.cuda.empty_cache()
+    per = {}
+    ferr = {}
+    shapes = []
+    for _, w in stream:
+        if tuple(w.n) not in shapes:
+            shapes.append(tuple(w.n))
+            per_w = w
+            for prec in ("fp64", "fp32"):
+                st = setup_workload(per_w, prec)
+                nsteps = 100
+                st.relax(tol=1e-30, max_steps=5, allow_unconverged=True)          # warm-up
+                st.set_m(W.to_soa(per_w.m0))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                k, _, _, _ = st.relax(tol=1e-30, max_steps=nsteps, allow_unconverged=True)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                a = per.setdefault(prec, [0.0, 0.0])
+                a[0] += per_w.ncells * k
+                a[1] += el
+                st.close()
+            s64 = setup_workload(per_w, "fp64")
+            s32 = setup_workload(per_w, "fp32")
+            h64 = s64.heff().double()
+            h32 = s32.heff().double()
+            ferr["%dx%dx%d" % tuple(per_w.n)] = float((h32 - h64).abs().max() / h64.abs().max())
+            s64.close()
+            s32.close()
+        if len(shapes) == len(W.SERVING_GRIDS):
+            break
+    summ["per_solve"] = {prec: {"cell_steps_per_s": v[0] / v[1],
+                                "sample": "100 DP45 steps of mm_relax on one request of each shape"}
+                         for prec, v in per.items()}
+    summ["served_vs_fp64_per_solve"] = summ["cell_steps_per_s"] / summ["per_solve"]["fp64"]["cell_steps_per_s"]
+    summ["fp32_field_rel_err_vs_fp64"] = ferr
+    return summ
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -396,6 +456,8 @@ def run_ours(args):
                       "l2": "per-stage working set ~0.7 GB > 129 MB L2, no flush"},
            "roofline": roof, "stage_roofline": stage_roof, "kernels": kernels32,
            "gpu_launches": launches, "e2e": e2e, "fp64": fp64, "clocks": clocks}
+    if args.serve_requests > 0 and ws == 1:
+        out["serving"] = serve_measure(torch, args.serve_requests)
     if cpu is not None:
         out["cpu_baseline"] = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stage of the FP64 oracle on the "
                                                   "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")
@@ -453,6 +515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the served stream to run (512 = all; 0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

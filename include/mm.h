@@ -202,20 +202,32 @@ void mm_batch_destroy(mm_batch* b);
 mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double alpha, const void* m0,
                             int on_device, double dt0);
 
-/* Free a slot (any state). */
+/* Free a slot (any state); its next request may be loaded at once. */
 mm_status mm_batch_clear_slot(mm_batch* b, int slot);
 
-/* Enqueue one DP45 attempt for every running slot (and the first-stage
- * evaluation of newly loaded slots); asynchronous. */
-mm_status mm_batch_begin(mm_batch* b, double rtol);
+/* Enqueue `attempts` (1..1024) consecutive DP45 attempts for every running
+ * slot, asynchronously on the batch's stream, preceded by the first-stage
+ * evaluation of newly loaded slots.  Every decision is taken on the device,
+ * per slot, with mm_llg_step's DP45 rule (error norm with atol = rtol, accept
+ * if err <= 1, dt <- dt min(5, max(0.2, 0.9 err^-1/5))): a slot whose torque
+ * max |m x h| / Ms falls below tol becomes 2 (converged) and takes no further
+ * steps, 3 = max_steps accepted steps reached, 4 = failed (non-finite values
+ * or step underflow).  The attempts are captured once per (number of launched
+ * slots, attempts, rtol, tol, max_steps) into a CUDA graph and replayed; a
+ * stream that cannot be captured (the legacy default stream) gets the same
+ * launches directly.  Slots may not be loaded, cleared or read until
+ * mm_batch_end. */
+mm_status mm_batch_begin(mm_batch* b, int attempts, double rtol, double tol, int max_steps);
 
-/* Wait for the attempt enqueued by mm_batch_begin, accept or reject it per
- * slot (same rule as mm_llg_step's DP45), and enqueue the accepted updates.
- * A slot whose torque falls below tol becomes 2 (converged); 3 = max_steps
- * accepted steps reached; 4 = failed (non-finite values or step underflow).
- * status/steps/torque: host arrays of `capacity` entries or NULL; status 0 is
- * an empty slot, 1 a running one. */
-mm_status mm_batch_end(mm_batch* b, double tol, int max_steps, int* status, int* steps, double* torque);
+/* Non-blocking: *ready = 1 once the work of mm_batch_begin has finished on
+ * the device (mm_batch_end will not wait), else 0.  MM_EINVAL if nothing is in
+ * flight. */
+mm_status mm_batch_query(mm_batch* b, int* ready);
+
+/* Wait for the work of mm_batch_begin and report every slot: status (0 empty,
+ * 1 running, 2/3/4 as above), accepted steps and last torque; host arrays of
+ * `capacity` entries or NULL.  MM_EINVAL if nothing is in flight. */
+mm_status mm_batch_end(mm_batch* b, int* status, int* steps, double* torque);
 
 /* Copy a slot's magnetisation out (host copies synchronise). */
 mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);

@@ -26,7 +26,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
-           "mm_batch_begin", "mm_batch_end", "mm_batch_get_m")
+           "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m")
 
 
 class MMError(RuntimeError):
@@ -91,8 +91,9 @@ def lib():
         "mm_batch_destroy": (None, [vp]),
         "mm_batch_set_slot": (i, [vp, i, d, d, d, vp, i, d]),
         "mm_batch_clear_slot": (i, [vp, i]),
-        "mm_batch_begin": (i, [vp, d]),
-        "mm_batch_end": (i, [vp, d, i, vp, vp, vp]),
+        "mm_batch_begin": (i, [vp, i, d, d, i]),
+        "mm_batch_query": (i, [vp, vp]),
+        "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
     for name, (res, args) in sig.items():
@@ -334,8 +335,8 @@ class State:
 
 
 class Batch:
-    """mm_batch: up to `capacity` same-shape grids relaxed together (one DP45
-    attempt for all running slots per begin/end pair)."""
+    """mm_batch: up to `capacity` same-shape grids relaxed together (`attempts`
+    DP45 attempts of all running slots per begin/end pair)."""
 
     def __init__(self, n, dx, precision="fp32", capacity=8, p=20, stream=None):
         import torch
@@ -384,12 +385,17 @@ class Batch:
     def clear_slot(self, slot):
         check(lib().mm_batch_clear_slot(self.h, int(slot)))
 
-    def begin(self, rtol=1e-5):
-        check(lib().mm_batch_begin(self.h, float(rtol)))
+    def begin(self, attempts=1, rtol=1e-5, tol=1e-3, max_steps=20000):
+        check(lib().mm_batch_begin(self.h, int(attempts), float(rtol), float(tol), int(max_steps)))
 
-    def end(self, tol=1e-3, max_steps=20000):
-        check(lib().mm_batch_end(self.h, float(tol), int(max_steps), self._status.ctypes.data,
-                                 self._steps.ctypes.data, self._torque.ctypes.data))
+    def ready(self):
+        r = ctypes.c_int(0)
+        check(lib().mm_batch_query(self.h, ctypes.byref(r)))
+        return bool(r.value)
+
+    def end(self):
+        check(lib().mm_batch_end(self.h, self._status.ctypes.data, self._steps.ctypes.data,
+                                 self._torque.ctypes.data))
         return self._status.copy(), self._steps.copy(), self._torque.copy()
 
     def get_m(self, slot):

@@ -143,6 +143,77 @@ template <typename T> __global__ void batch_accept_kernel(const T* __restrict__ 
     k1[o + i] = k7[o + i]; k1[o + N + i] = k7[o + N + i]; k1[o + 2 * N + i] = k7[o + 2 * N + i];
 }
 
+// ---- device-side Dormand-Prince controller (one thread per slot) ----------
+// Slot status: 0 empty, 1 running, 2 converged, 3 max steps, 4 failed.
+
+// mask[0..cap): running and not yet evaluated; mask[cap..2cap): running
+__global__ void batch_masks_kernel(const int* __restrict__ status, const int* __restrict__ fresh,
+                                   int* __restrict__ mask, int cap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        const int run = status[i] == 1;
+        mask[i] = run && fresh[i];
+        mask[cap + i] = run;
+    }
+}
+
+// after the first-stage evaluation of fresh slots: their initial torque (a
+// slot already below tol converges without a step) or failure
+__global__ void batch_first_kernel(const double* __restrict__ scal, const int* __restrict__ fmask,
+                                   int* __restrict__ status, int* __restrict__ fresh, double* __restrict__ torque,
+                                   double tol, int cap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        if (!fmask[i]) continue;
+        fresh[i] = 0;
+        const double tq = scal[3 * i], nf = scal[3 * i + 2];
+        if (nf != 0.0 || !isfinite(tq)) { status[i] = 4; continue; }
+        torque[i] = tq;
+        if (tq < tol) status[i] = 2;
+    }
+}
+
+// one attempt's outcome per running slot: accept (err <= 1) or reject, the
+// next step size dt * min(5, max(0.2, 0.9 err^-1/5)), the time, the step count
+// and the status; acc[i] selects the slots whose solution is taken, and the
+// running mask is updated for the next attempt
+__global__ void batch_control_kernel(const double* __restrict__ scal, int* __restrict__ run,
+                                     int* __restrict__ status, int* __restrict__ steps, double* __restrict__ dt,
+                                     double* __restrict__ t, double* __restrict__ torque, int* __restrict__ acc,
+                                     double tol, int max_steps, int cap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        acc[i] = 0;
+        if (!run[i]) continue;
+        const double tq = scal[3 * i], err = scal[3 * i + 1], nf = scal[3 * i + 2];
+        if (nf != 0.0 || !isfinite(err)) { status[i] = 4; run[i] = 0; continue; }
+        const double f = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+        if (err <= 1.0) {
+            acc[i] = 1;
+            t[i] += dt[i];
+            steps[i] += 1;
+            torque[i] = tq;
+            dt[i] *= f;
+            if (tq < tol) status[i] = 2;
+            else if (steps[i] >= max_steps) status[i] = 3;
+        } else {
+            dt[i] *= f;
+            if (!(dt[i] >= 1e-22)) status[i] = 4;
+        }
+        run[i] = status[i] == 1;
+    }
+}
+
+void launch_batch_masks(const int* status, const int* fresh, int* mask, int cap, cudaStream_t st) {
+    batch_masks_kernel<<<(cap + 127) / 128, 128, 0, st>>>(status, fresh, mask, cap);
+}
+void launch_batch_first(const double* scal, const int* fmask, int* status, int* fresh, double* torque, double tol,
+                        int cap, cudaStream_t st) {
+    batch_first_kernel<<<(cap + 127) / 128, 128, 0, st>>>(scal, fmask, status, fresh, torque, tol, cap);
+}
+void launch_batch_control(const double* scal, int* run, int* status, int* steps, double* dt, double* t,
+                          double* torque, int* acc, double tol, int max_steps, int cap, cudaStream_t st) {
+    batch_control_kernel<<<(cap + 127) / 128, 128, 0, st>>>(scal, run, status, steps, dt, t, torque, acc, tol,
+                                                            max_steps, cap);
+}
+
 template <typename T> void launch_batch_stage(const BatchStageParams<T>& p, cudaStream_t st) {
     dim3 grid((p.N + 255) / 256, p.nb);
     batch_stage_kernel<T><<<grid, 256, 0, st>>>(p);

@@ -34,6 +34,11 @@ template <typename T> void launch_batch_stage(const BatchStageParams<T>& p, cuda
 void launch_batch_finalize(const double* partials, int nblk, int nb, double* scalars, cudaStream_t st);
 template <typename T> void launch_batch_combine(const T* m, const T* k, const double* dt, double a, const int* mask,
                                                 T* out, int N, int nb, cudaStream_t st);
+void launch_batch_masks(const int* status, const int* fresh, int* mask, int cap, cudaStream_t st);
+void launch_batch_first(const double* scal, const int* fmask, int* status, int* fresh, double* torque, double tol,
+                        int cap, cudaStream_t st);
+void launch_batch_control(const double* scal, int* run, int* status, int* steps, double* dt, double* t,
+                          double* torque, int* acc, double tol, int max_steps, int cap, cudaStream_t st);
 template <typename T> void launch_batch_accept(const T* y5, const T* k7, const int* acc, T* m, T* k1, int N, int nb,
                                                cudaStream_t st);
 

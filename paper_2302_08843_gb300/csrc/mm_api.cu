@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "adjoint.h"
@@ -632,23 +633,33 @@ struct mm_batch {
     void* Ms_d = nullptr;
     void* A_d = nullptr;
     void* alpha_d = nullptr;
-    double* dt_d = nullptr;
-    int* mask_d = nullptr;       // [2][cap]: first-stage mask, attempt mask
+    // per-slot controller state, on the device: status, steps, fresh, dt, t, torque
+    int* ctl_i = nullptr;        // [3][cap] ints
+    double* ctl_d = nullptr;     // [3][cap] doubles
+    int* mask_d = nullptr;       // [2][cap]: first-stage mask, running mask
     int* acc_d = nullptr;
     double* partials = nullptr;
     int nblk = 0;
     double* scal_d = nullptr;    // [2][cap][3]: first stage, attempt
-    double* scal_h = nullptr;    // pinned mirror
-    int* mask_h = nullptr;       // pinned [2][cap]
-    int* acc_h = nullptr;        // pinned [cap]
-    double* dt_h = nullptr;      // pinned [cap]
-    int y5 = 0;                  // which Y buffer holds the last attempt's fifth-order solution
+    int* rep_i = nullptr;        // pinned report: status, steps
+    double* rep_d = nullptr;     // pinned report: torque
+    cudaEvent_t done = nullptr;  // recorded after the report copy of mm_batch_begin
+    int y5 = 0;                  // which Y buffer holds an attempt's fifth-order solution
     int nact = 0;                // slots [0, nact) are launched (highest running slot + 1)
-    double rtol = 1e-5;
     bool pending = false;
-    std::vector<int> status, steps;
-    std::vector<double> t, dt, torque, Ms, A, alpha;
-    std::vector<char> fresh;     // first stage not evaluated yet
+    bool fresh_any = false;
+    std::vector<int> status;     // host mirror of the last report
+    // cached CUDA graphs of `attempts` consecutive attempts, per (nact, attempts)
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    double g_rtol = -1, g_tol = -1;
+    int g_max_steps = -1;
+
+    int* status_d() { return ctl_i; }
+    int* steps_d() { return ctl_i + cap; }
+    int* fresh_d() { return ctl_i + 2 * cap; }
+    double* dt_d() { return ctl_d; }
+    double* t_d() { return ctl_d + cap; }
+    double* torque_d() { return ctl_d + 2 * cap; }
 };
 
 namespace {
@@ -666,13 +677,14 @@ size_t batch_bytes(const mm_grid* g, mm_precision prec, int cap, int* LXo, int* 
     if (LY > 1) bytes += (size_t)cap * 3 * csz * g->nz * LY * KXS;              // S2
     bytes += 6 * rsz * (size_t)(LZ / 2 + 1) * (LY / 2 + 1) * KXS;               // tensor
     const size_t nblk = (N + 255) / 256;
-    bytes += (size_t)cap * (nblk * 3 * 8 + 3 * rsz + 8 + 3 * 4 + 2 * 3 * 8);
+    bytes += (size_t)cap * (2 * nblk * 3 * 8 + 3 * rsz + 3 * 4 + 3 * 8 + 2 * 4 + 4 + 2 * 3 * 8);
     if (LXo) { *LXo = LX; *LYo = LY; *LZo = LZ; *KXSo = KXS; }
     return bytes;
 }
 
 template <typename T> mm_status batch_stage(mm_batch* b, const void* m, const void* mn, void* k_out, void* next,
-                                            const int* mask, int st, bool err, bool torque, double* partials) {
+                                            const int* mask, int st, bool err, bool torque, double* partials,
+                                            double rtol) {
     BatchStageParams<T> p;
     std::memset(&p, 0, sizeof(p));
     p.nx = b->g.nx; p.ny = b->g.ny; p.nz = b->g.nz; p.N = (int)b->N; p.nb = b->nact;
@@ -680,7 +692,7 @@ template <typename T> mm_status batch_stage(mm_batch* b, const void* m, const vo
     p.idy2 = (T)(1.0 / (b->g.dy * b->g.dy));
     p.idz2 = (T)(1.0 / (b->g.dz * b->g.dz));
     p.Ms = (const T*)b->Ms_d; p.A = (const T*)b->A_d; p.alpha = (const T*)b->alpha_d;
-    p.dt = b->dt_d;
+    p.dt = b->dt_d();
     p.mask = mask;
     p.m = (const T*)m; p.hd = (const T*)b->hd; p.mn = (const T*)mn;
     p.k_out = (T*)k_out; p.next = (T*)next;
@@ -698,7 +710,7 @@ template <typename T> mm_status batch_stage(mm_batch* b, const void* m, const vo
     p.want_err = err;
     p.want_torque = torque;
     p.partials = partials;
-    p.rtol = b->rtol;
+    p.rtol = rtol;
     launch_batch_stage<T>(p, b->st);
     MM_LAUNCHED();
     return MM_OK;
@@ -712,96 +724,109 @@ template <typename T> mm_status batch_demag(mm_batch* b, const void* m) {
     return MM_OK;
 }
 
-template <typename T> mm_status batch_begin_impl(mm_batch* b, double rtol) {
+// first-stage derivative k1 = f(m) and initial torque of newly loaded slots
+template <typename T> mm_status batch_first(mm_batch* b, double rtol, double tol) {
     const int cap = b->cap;
-    b->rtol = rtol;
-    int nnew = 0, nrun = 0, hi = 0;
-    for (int i = 0; i < cap; ++i) {
-        b->mask_h[i] = (b->status[i] == 1 && b->fresh[i]) ? 1 : 0;
-        b->mask_h[cap + i] = b->status[i] == 1 ? 1 : 0;
-        b->dt_h[i] = b->dt[i];
-        nnew += b->mask_h[i];
-        nrun += b->mask_h[cap + i];
-        if (b->status[i] == 1) hi = i + 1;
-    }
-    b->pending = nrun > 0;
-    if (!nrun) return MM_OK;
-    // grids past the highest running slot are not launched at all; the
-    // masked ones below it cost one early-exiting block per tile
-    b->nact = hi;
-    b->d.nb = hi;
-    MM_CUDA(cudaMemcpyAsync(b->mask_d, b->mask_h, sizeof(int) * 2 * cap, cudaMemcpyHostToDevice, b->st));
-    MM_CUDA(cudaMemcpyAsync(b->dt_d, b->dt_h, sizeof(double) * cap, cudaMemcpyHostToDevice, b->st));
-    double* p0 = b->partials;
-    double* p1 = b->partials + (size_t)cap * b->nblk * 3;
-    if (nnew) {
-        // k1 = f(m) and the initial torque of newly loaded slots
-        MM_TRY(batch_demag<T>(b, b->m));
-        MM_TRY(batch_stage<T>(b, b->m, b->m, b->K[0], nullptr, b->mask_d, 0, false, true, p0));
-        launch_batch_finalize(p0, b->nblk, hi, b->scal_d, b->st);
-        MM_LAUNCHED();
-    }
-    const int* run = b->mask_d + cap;
-    launch_batch_combine<T>((const T*)b->m, (const T*)b->K[0], b->dt_d, kDP_A[1][0], run, (T*)b->Y[0], (int)b->N,
-                            hi, b->st);
+    launch_batch_masks(b->status_d(), b->fresh_d(), b->mask_d, cap, b->st);
     MM_LAUNCHED();
-    int cur = 0;
-    for (int st = 1; st <= 6; ++st) {
-        MM_TRY(batch_demag<T>(b, b->Y[cur]));
-        if (st < 6) {
-            MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[st], b->Y[1 - cur], run, st, false, false, nullptr));
-            cur = 1 - cur;
-        } else {
-            MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[6], nullptr, run, 6, true, true, p1));
-            b->y5 = cur;
-        }
-    }
-    launch_batch_finalize(p1, b->nblk, hi, b->scal_d + 3 * cap, b->st);
+    MM_TRY(batch_demag<T>(b, b->m));
+    MM_TRY(batch_stage<T>(b, b->m, b->m, b->K[0], nullptr, b->mask_d, 0, false, true, b->partials, rtol));
+    launch_batch_finalize(b->partials, b->nblk, b->nact, b->scal_d, b->st);
     MM_LAUNCHED();
-    MM_CUDA(cudaMemcpyAsync(b->scal_h, b->scal_d, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, b->st));
+    launch_batch_first(b->scal_d, b->mask_d, b->status_d(), b->fresh_d(), b->torque_d(), tol, cap, b->st);
+    MM_LAUNCHED();
     return MM_OK;
 }
 
-template <typename T> mm_status batch_end_impl(mm_batch* b, double tol, int max_steps) {
+// `attempts` DP45 attempts of every running slot, all decisions on the device
+template <typename T> mm_status batch_attempts(mm_batch* b, int attempts, double rtol, double tol, int max_steps) {
     const int cap = b->cap;
-    if (!b->pending) return MM_OK;
-    MM_CUDA(cudaStreamSynchronize(b->st));
-    b->pending = false;
-    int nacc = 0;
-    for (int i = 0; i < cap; ++i) {
-        b->acc_h[i] = 0;
-        if (b->status[i] != 1) continue;
-        if (b->fresh[i]) {
-            b->fresh[i] = 0;
-            const double tq0 = b->scal_h[3 * i + 0];
-            if (b->scal_h[3 * i + 2] != 0.0 || !std::isfinite(tq0)) { b->status[i] = 4; continue; }
-            b->torque[i] = tq0;
-            if (tq0 < tol) { b->status[i] = 2; continue; }     // already relaxed: the attempt is discarded
+    int* run = b->mask_d + cap;
+    double* p1 = b->partials + (size_t)cap * b->nblk * 3;
+    launch_batch_masks(b->status_d(), b->fresh_d(), b->mask_d, cap, b->st);
+    MM_LAUNCHED();
+    for (int a = 0; a < attempts; ++a) {
+        launch_batch_combine<T>((const T*)b->m, (const T*)b->K[0], b->dt_d(), kDP_A[1][0], run, (T*)b->Y[0],
+                                (int)b->N, b->nact, b->st);
+        MM_LAUNCHED();
+        int cur = 0;
+        for (int st = 1; st <= 6; ++st) {
+            MM_TRY(batch_demag<T>(b, b->Y[cur]));
+            if (st < 6) {
+                MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[st], b->Y[1 - cur], run, st, false, false, nullptr,
+                                      rtol));
+                cur = 1 - cur;
+            } else {
+                MM_TRY(batch_stage<T>(b, b->Y[cur], b->m, b->K[6], nullptr, run, 6, true, true, p1, rtol));
+                b->y5 = cur;
+            }
         }
-        const double tq = b->scal_h[3 * (cap + i) + 0];
-        const double err = b->scal_h[3 * (cap + i) + 1];
-        if (b->scal_h[3 * (cap + i) + 2] != 0.0 || !std::isfinite(err)) { b->status[i] = 4; continue; }
-        const double f = dp_factor(err);
-        if (err <= 1.0) {
-            b->acc_h[i] = 1;
-            ++nacc;
-            b->t[i] += b->dt[i];
-            b->steps[i] += 1;
-            b->torque[i] = tq;
-            b->dt[i] *= f;
-            if (tq < tol) b->status[i] = 2;
-            else if (b->steps[i] >= max_steps) b->status[i] = 3;
-        } else {
-            b->dt[i] *= f;
-            if (!(b->dt[i] >= 1e-22)) b->status[i] = 4;
-        }
-    }
-    if (nacc) {
-        MM_CUDA(cudaMemcpyAsync(b->acc_d, b->acc_h, sizeof(int) * cap, cudaMemcpyHostToDevice, b->st));
-        launch_batch_accept<T>((const T*)b->Y[b->y5], (const T*)b->K[6], b->acc_d, (T*)b->m, (T*)b->K[0], (int)b->N,
-                               b->nact, b->st);
+        launch_batch_finalize(p1, b->nblk, b->nact, b->scal_d + 3 * cap, b->st);
+        MM_LAUNCHED();
+        launch_batch_control(b->scal_d + 3 * cap, run, b->status_d(), b->steps_d(), b->dt_d(), b->t_d(),
+                             b->torque_d(), b->acc_d, tol, max_steps, cap, b->st);
+        MM_LAUNCHED();
+        launch_batch_accept<T>((const T*)b->Y[b->y5], (const T*)b->K[6], b->acc_d, (T*)b->m, (T*)b->K[0],
+                               (int)b->N, b->nact, b->st);
         MM_LAUNCHED();
     }
+    return MM_OK;
+}
+
+void batch_drop_graphs(mm_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+template <typename T>
+mm_status batch_begin_impl(mm_batch* b, int attempts, double rtol, double tol, int max_steps) {
+    const int cap = b->cap;
+    int nrun = 0, hi = 0;
+    for (int i = 0; i < cap; ++i)
+        if (b->status[i] == 1) { ++nrun; hi = i + 1; }
+    b->pending = true;                         // the report copy below is always enqueued
+    if (nrun) {
+        // grids past the highest running slot are not launched at all; the
+        // masked ones below it cost one early-exiting block per tile
+        b->nact = hi;
+        b->d.nb = hi;
+        if (b->fresh_any) {
+            MM_TRY(batch_first<T>(b, rtol, tol));
+            b->fresh_any = false;
+        }
+        if (rtol != b->g_rtol || tol != b->g_tol || max_steps != b->g_max_steps) {
+            batch_drop_graphs(b);
+            b->g_rtol = rtol; b->g_tol = tol; b->g_max_steps = max_steps;
+        }
+        const auto key = std::make_pair(hi, attempts);
+        auto it = b->graphs.find(key);
+        cudaGraphExec_t exec = it == b->graphs.end() ? nullptr : it->second;
+        if (!exec) {
+            // capture once; a stream that cannot be captured (the legacy
+            // default stream) gets the same launches directly
+            cudaGraph_t graph = nullptr;
+            if (b->st && cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const mm_status cs = batch_attempts<T>(b, attempts, rtol, tol, max_steps);
+                const cudaError_t ce = cudaStreamEndCapture(b->st, &graph);
+                if (cs != MM_OK || ce != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    return cs != MM_OK ? cs : fail(MM_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+                }
+                const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ie != cudaSuccess) return fail(MM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+                b->graphs[key] = exec;
+            } else {
+                cudaGetLastError();
+                MM_TRY(batch_attempts<T>(b, attempts, rtol, tol, max_steps));
+            }
+        }
+        if (exec) MM_CUDA(cudaGraphLaunch(exec, b->st));
+    }
+    MM_CUDA(cudaMemcpyAsync(b->rep_i, b->ctl_i, sizeof(int) * 2 * cap, cudaMemcpyDeviceToHost, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->rep_d, b->torque_d(), sizeof(double) * cap, cudaMemcpyDeviceToHost, b->st));
+    MM_CUDA(cudaEventRecord(b->done, b->st));
     return MM_OK;
 }
 
@@ -1055,16 +1080,16 @@ void mm_batch_destroy(mm_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->st);
+    batch_drop_graphs(b);
     void** bufs[] = {&b->m, &b->Y[0], &b->Y[1], &b->hd, &b->S1, &b->S2, &b->tens, &b->Ms_d, &b->A_d, &b->alpha_d,
-                     reinterpret_cast<void**>(&b->dt_d), reinterpret_cast<void**>(&b->mask_d),
-                     reinterpret_cast<void**>(&b->acc_d), reinterpret_cast<void**>(&b->partials),
-                     reinterpret_cast<void**>(&b->scal_d)};
+                     reinterpret_cast<void**>(&b->ctl_i), reinterpret_cast<void**>(&b->ctl_d),
+                     reinterpret_cast<void**>(&b->mask_d), reinterpret_cast<void**>(&b->acc_d),
+                     reinterpret_cast<void**>(&b->partials), reinterpret_cast<void**>(&b->scal_d)};
     for (void** q : bufs) dev_free(*q);
     for (int q = 0; q < 7; ++q) dev_free(b->K[q]);
-    if (b->scal_h) cudaFreeHost(b->scal_h);
-    if (b->mask_h) cudaFreeHost(b->mask_h);
-    if (b->acc_h) cudaFreeHost(b->acc_h);
-    if (b->dt_h) cudaFreeHost(b->dt_h);
+    if (b->rep_i) cudaFreeHost(b->rep_i);
+    if (b->rep_d) cudaFreeHost(b->rep_d);
+    if (b->done) cudaEventDestroy(b->done);
     delete b;
 }
 
@@ -1109,7 +1134,9 @@ mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capac
     if ((st = dev_alloc(&b->Ms_d, b->rsz * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(&b->A_d, b->rsz * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(&b->alpha_d, b->rsz * capacity)) != MM_OK) return bail(st);
-    if ((st = dev_alloc(reinterpret_cast<void**>(&b->dt_d), sizeof(double) * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->ctl_i), sizeof(int) * 3 * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->ctl_d), sizeof(double) * 3 * capacity)) != MM_OK)
+        return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&b->mask_d), sizeof(int) * 2 * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&b->acc_d), sizeof(int) * capacity)) != MM_OK) return bail(st);
     b->nblk = (int)((b->N + 255) / 256);
@@ -1117,11 +1144,11 @@ mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capac
         MM_OK)
         return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&b->scal_d), sizeof(double) * 6 * capacity)) != MM_OK) return bail(st);
-    if (cudaMallocHost(reinterpret_cast<void**>(&b->scal_h), sizeof(double) * 6 * capacity) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&b->mask_h), sizeof(int) * 2 * capacity) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&b->acc_h), sizeof(int) * capacity) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&b->dt_h), sizeof(double) * capacity) != cudaSuccess)
+    if (cudaMallocHost(reinterpret_cast<void**>(&b->rep_i), sizeof(int) * 2 * capacity) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->rep_d), sizeof(double) * capacity) != cudaSuccess)
         return bail(fail(MM_ENOMEM, "cudaMallocHost"));
+    if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(fail(MM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
     b->d.Ms_b = b->Ms_d;
     // the size bucket's plan: tensor spectrum of this shape, shared by every slot
     const int n[3] = {grid->nx, grid->ny, grid->nz};
@@ -1141,17 +1168,11 @@ mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capac
     if (e == cudaSuccess && s2) e = cudaMemsetAsync(b->S2, 0, s2, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->m, 0, v3, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->Ms_d, 0, b->rsz * capacity, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl_i, 0, sizeof(int) * 3 * capacity, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl_d, 0, sizeof(double) * 3 * capacity, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return bail(fail(MM_ECUDA, "batch set-up: %s", cudaGetErrorString(e)));
     b->status.assign(capacity, 0);
-    b->steps.assign(capacity, 0);
-    b->t.assign(capacity, 0.0);
-    b->dt.assign(capacity, 1e-13);
-    b->torque.assign(capacity, 0.0);
-    b->Ms.assign(capacity, 0.0);
-    b->A.assign(capacity, 0.0);
-    b->alpha.assign(capacity, 0.0);
-    b->fresh.assign(capacity, 0);
     *out = b;
     return MM_OK;
 }
@@ -1160,6 +1181,7 @@ mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double a
                             double dt0) {
     if (!b || !m0) return fail(MM_EINVAL, "null argument");
     if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    if (b->pending) return fail(MM_EINVAL, "attempts are in flight: call mm_batch_end first");
     if (b->status[slot] != 0) return fail(MM_EINVAL, "slot %d is busy", slot);
     if (!(Ms >= 0) || !(A >= 0) || !(alpha >= 0)) return fail(MM_EINVAL, "bad material");
     MM_CUDA(cudaSetDevice(b->device));
@@ -1176,42 +1198,68 @@ mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double a
             MM_CUDA(cudaMemcpyAsync(static_cast<float*>(dst[q]) + slot, &f, 4, cudaMemcpyHostToDevice, b->st));
         }
     }
+    const int one = 1, zero = 0;
+    const double dt = dt0 > 0 ? dt0 : 1e-13, dz = 0.0;
+    MM_CUDA(cudaMemcpyAsync(b->status_d() + slot, &one, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->steps_d() + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->fresh_d() + slot, &one, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->dt_d() + slot, &dt, sizeof(double), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->t_d() + slot, &dz, sizeof(double), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->torque_d() + slot, &dz, sizeof(double), cudaMemcpyHostToDevice, b->st));
     MM_CUDA(cudaStreamSynchronize(b->st));   // the host values above are stack copies
     b->status[slot] = 1;
-    b->steps[slot] = 0;
-    b->t[slot] = 0.0;
-    b->dt[slot] = dt0 > 0 ? dt0 : 1e-13;
-    b->torque[slot] = 0.0;
-    b->Ms[slot] = Ms; b->A[slot] = A; b->alpha[slot] = alpha;
-    b->fresh[slot] = 1;
+    b->fresh_any = true;
     return MM_OK;
 }
 
 mm_status mm_batch_clear_slot(mm_batch* b, int slot) {
     if (!b) return fail(MM_EINVAL, "null batch");
     if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
-    if (b->pending) return fail(MM_EINVAL, "an attempt is in flight: call mm_batch_end first");
+    if (b->pending) return fail(MM_EINVAL, "attempts are in flight: call mm_batch_end first");
+    MM_CUDA(cudaSetDevice(b->device));
+    const int zero = 0;
+    MM_CUDA(cudaMemcpyAsync(b->status_d() + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaMemcpyAsync(b->fresh_d() + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaStreamSynchronize(b->st));
     b->status[slot] = 0;
-    b->fresh[slot] = 0;
     return MM_OK;
 }
 
-mm_status mm_batch_begin(mm_batch* b, double rtol) {
+mm_status mm_batch_begin(mm_batch* b, int attempts, double rtol, double tol, int max_steps) {
     if (!b) return fail(MM_EINVAL, "null batch");
-    if (!(rtol > 0)) return fail(MM_EINVAL, "rtol must be > 0");
-    if (b->pending) return fail(MM_EINVAL, "an attempt is already in flight");
+    if (attempts < 1 || attempts > 1024) return fail(MM_EINVAL, "attempts must be in 1..1024");
+    if (!(rtol > 0) || !(tol >= 0) || max_steps < 1) return fail(MM_EINVAL, "bad rtol, tol or max_steps");
+    if (b->pending) return fail(MM_EINVAL, "attempts are already in flight");
     MM_CUDA(cudaSetDevice(b->device));
-    return b->prec == MM_FP64 ? batch_begin_impl<double>(b, rtol) : batch_begin_impl<float>(b, rtol);
+    return b->prec == MM_FP64 ? batch_begin_impl<double>(b, attempts, rtol, tol, max_steps)
+                              : batch_begin_impl<float>(b, attempts, rtol, tol, max_steps);
 }
 
-mm_status mm_batch_end(mm_batch* b, double tol, int max_steps, int* status, int* steps, double* torque) {
-    if (!b) return fail(MM_EINVAL, "null batch");
+mm_status mm_batch_query(mm_batch* b, int* ready) {
+    if (!b || !ready) return fail(MM_EINVAL, "null argument");
+    if (!b->pending) return fail(MM_EINVAL, "nothing in flight: call mm_batch_begin first");
     MM_CUDA(cudaSetDevice(b->device));
-    MM_TRY(b->prec == MM_FP64 ? batch_end_impl<double>(b, tol, max_steps) : batch_end_impl<float>(b, tol, max_steps));
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady) {
+        *ready = 0;
+        return MM_OK;
+    }
+    MM_CUDA(e);
+    *ready = 1;
+    return MM_OK;
+}
+
+mm_status mm_batch_end(mm_batch* b, int* status, int* steps, double* torque) {
+    if (!b) return fail(MM_EINVAL, "null batch");
+    if (!b->pending) return fail(MM_EINVAL, "nothing in flight: call mm_batch_begin first");
+    MM_CUDA(cudaSetDevice(b->device));
+    b->pending = false;
+    MM_CUDA(cudaStreamSynchronize(b->st));
     for (int i = 0; i < b->cap; ++i) {
-        if (status) status[i] = b->status[i];
-        if (steps) steps[i] = b->steps[i];
-        if (torque) torque[i] = b->torque[i];
+        b->status[i] = b->rep_i[i];
+        if (status) status[i] = b->rep_i[i];
+        if (steps) steps[i] = b->rep_i[b->cap + i];
+        if (torque) torque[i] = b->rep_d[i];
     }
     return MM_OK;
 }
@@ -1219,6 +1267,7 @@ mm_status mm_batch_end(mm_batch* b, double tol, int max_steps, int* status, int*
 mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device) {
     if (!b || !m_out) return fail(MM_EINVAL, "null argument");
     if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    if (b->pending) return fail(MM_EINVAL, "attempts are in flight: call mm_batch_end first");
     MM_CUDA(cudaSetDevice(b->device));
     const size_t v = 3 * b->rsz * (size_t)b->N;
     MM_CUDA(cudaMemcpyAsync(m_out, static_cast<char*>(b->m) + slot * v, v,

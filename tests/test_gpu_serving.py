@@ -19,16 +19,16 @@ def _req(rng, n, name="r", dx=(3e-9, 3e-9, 3e-9)):
                     alpha=1.0, m0=m0)
 
 
-def _drive(b, tol, max_steps):
+def _drive(b, tol, max_steps, attempts=1):
     while True:
-        b.begin(1e-5)
-        st, steps, tq = b.end(tol, max_steps)
+        b.begin(attempts, 1e-5, tol, max_steps)
+        st, steps, tq = b.end()
         if not np.any(st == 1):
             return st, steps, tq
 
 
-@pytest.mark.parametrize("n", [(7, 5, 3), (12, 8, 2)])
-def test_batched_relax_fp64_matches_oracle(n):
+@pytest.mark.parametrize("n,attempts", [((7, 5, 3), 1), ((12, 8, 2), 7)])
+def test_batched_relax_fp64_matches_oracle(n, attempts):
     from oracle.llg import relax
     from paper_2302_08843_gb300.binding import Batch
     from paper_2302_08843_gb300.workloads import from_soa, to_soa
@@ -37,7 +37,7 @@ def test_batched_relax_fp64_matches_oracle(n):
     b = Batch(n, reqs[0].dx, "fp64", capacity=4)
     for slot, w in zip((0, 2, 3), reqs):      # slot 1 stays empty
         b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
-    st, steps, tq = _drive(b, 1e-3, 5000)
+    st, steps, tq = _drive(b, 1e-3, 5000, attempts)
     assert st[1] == 0
     for slot, w in zip((0, 2, 3), reqs):
         mr, steps_r, tq_r, _ = relax(oracle_problem(w), w.m0, tol=1e-3, max_steps=5000)
@@ -55,16 +55,22 @@ def test_batched_fixed_steps_fp32_vs_fp64_oracle():
     rng = np.random.default_rng(22)
     n = (16, 8, 2)
     reqs = [_req(rng, n) for _ in range(2)]
-    b = Batch(n, reqs[0].dx, "fp32", capacity=2)
-    for slot, w in enumerate(reqs):
-        b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
-    st, steps, _ = _drive(b, 1e-12, 20)      # unreachable tolerance: 20 accepted steps each
-    for slot, w in enumerate(reqs):
-        mr, steps_r, _, _ = relax(oracle_problem(w), w.m0, tol=1e-12, max_steps=20)
-        assert st[slot] == 3 and steps[slot] == steps_r == 20
-        # per field evaluation the FP32 path is within 1e-5; 20 steps accumulate it
-        assert rel(from_soa(b.get_m(slot)), mr) < 20 * FP32_TOL
-    b.close()
+    out = []
+    for attempts in (1, 13):              # direct launches of one attempt vs a graph of 13
+        b = Batch(n, reqs[0].dx, "fp32", capacity=2)
+        for slot, w in enumerate(reqs):
+            b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
+        st, steps, _ = _drive(b, 1e-12, 20, attempts)     # unreachable tolerance: 20 accepted steps each
+        out.append([b.get_m(slot) for slot in range(2)])
+        for slot, w in enumerate(reqs):
+            mr, steps_r, _, _ = relax(oracle_problem(w), w.m0, tol=1e-12, max_steps=20)
+            assert st[slot] == 3 and steps[slot] == steps_r == 20
+            # per field evaluation the FP32 path is within 1e-5; 20 steps accumulate it
+            assert rel(from_soa(out[-1][slot]), mr) < 20 * FP32_TOL
+        b.close()
+    # a slot stops at max_steps inside a graph: both runs are bitwise the same
+    for a, c in zip(out[0], out[1]):
+        assert np.array_equal(a, c)
 
 
 def test_relaxed_at_start_converges_without_steps():

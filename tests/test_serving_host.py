@@ -41,15 +41,19 @@ class FakeBatch:
         self.steps[slot] = 0
         self.status[slot] = 1
 
-    def begin(self, rtol=1e-5):
-        pass
+    def begin(self, attempts=1, rtol=1e-5, tol=1e-3, max_steps=20000):
+        self.attempts = attempts
 
-    def end(self, tol=1e-3, max_steps=20000):
+    def ready(self):
+        return True
+
+    def end(self):
         for s in range(self.capacity):
-            if self.status[s] == 1:
-                self.steps[s] += 1
-                if self.steps[s] >= self.need[s]:
-                    self.status[s] = 2
+            for _ in range(self.attempts):
+                if self.status[s] == 1:
+                    self.steps[s] += 1
+                    if self.steps[s] >= self.need[s]:
+                        self.status[s] = 2
         return (np.array(self.status, dtype=np.int32), np.array(self.steps, dtype=np.int32),
                 np.zeros(self.capacity))
 
@@ -125,6 +129,16 @@ def test_oversize_request_rejected(fake):
     s = latency_summary(res, srv.elapsed)
     assert s["rejected"] == 1
     srv.close()
+
+
+def test_auto_capacity():
+    from paper_2302_08843_gb300.serving import auto_capacity
+    assert auto_capacity((64, 64, 1)) == 32
+    assert auto_capacity((100, 100, 8)) == 16
+    assert auto_capacity((256, 256, 64)) == 4
+    for n in [(1, 1, 1), (7, 5, 3), (512, 512, 8)]:
+        c = auto_capacity(n)
+        assert 4 <= c <= 32 and c & (c - 1) == 0
 
 
 def test_realtime_arrivals_wait_for_their_time(fake):
