@@ -22,6 +22,7 @@
 
 #include <cstdio>
 #include <mutex>
+#include <utility>
 
 #include "demag.h"
 #include "fft_engine.cuh"
@@ -293,16 +294,19 @@ p5_x_tma(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float* __restr
 // update reads it there, writes acc/next to global memory and puts Ms * next
 // back in the same place, which the forward transform then turns into the
 // next stage's x-spectrum, written over this tile's rows of S1.
-template <int LX, int TY>
-__global__ void __launch_bounds__((3 * TY / 2) * Fft<float, LX, +1, false>::TPL, 2)
+// NSLOT TMA slots: with one, the next tile's load is issued as soon as this
+// tile is staged and has both transforms and the cell updates to land.
+template <int LX, int TY, int NSLOT, int PAD, int MINB>
+__global__ void __launch_bounds__((3 * TY / 2) * Fft<float, LX, +1, false>::TPL, MINB)
 k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __restrict__ S1, StageParams<float> p,
          int kxb, int nboxes, int slot_bytes) {
     using C = float2;
     using FI = Fft<float, LX, +1, false>;
     using FF = Fft<float, LX, -1, (LX > 1)>;
     static_assert(FI::TPL == FF::TPL, "engines must agree on threads per line");
+    static_assert(NSLOT == 1 || NSLOT == 2, "one or two TMA slots");
     constexpr int NL = 3 * TY / 2;
-    constexpr int LS = NL + 1;
+    constexpr int LS = NL + PAD;
     constexpr int NT = NL * FI::TPL;
     constexpr int KXn = LX / 2 + 1;
     constexpr int XH = LX / 2;
@@ -313,8 +317,8 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
     const int N = nx * ny * nz;
     const int nyt = (ny + TY - 1) / TY;
     const int ntiles = nyt * nz;
-    C* work = reinterpret_cast<C*>(smtma + 2 * (size_t)slot_bytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes + (size_t)LX * LS * sizeof(C));
+    C* work = reinterpret_cast<C*>(smtma + NSLOT * (size_t)slot_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + NSLOT * (size_t)slot_bytes + (size_t)LX * LS * sizeof(C));
     const uint32_t tx = (uint32_t)(nboxes * kxb * TY * 3 * sizeof(C));
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -322,6 +326,8 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
         fence_mbar_init();
     }
     __syncthreads();
+    grid_dep_launch();
+    grid_dep_wait();      // the previous pass's output is complete from here on
     auto issue = [&](int t, int sl) {
         const int yt = t % nyt, z = t / nyt;
         C* dst = reinterpret_cast<C*>(smtma + (size_t)sl * slot_bytes);
@@ -332,18 +338,20 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
     const int t0 = blockIdx.x;
     if (tid == 0) {
         if (t0 < ntiles) issue(t0, 0);
-        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+        if (NSLOT == 2 && t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
     }
     const float* m = p.m;
     int it = 0;
     for (int t = t0; t < ntiles; t += gridDim.x, ++it) {
-        const int sl = it & 1;
+        const int sl = NSLOT == 2 ? (it & 1) : 0;
+        const uint32_t par = NSLOT == 2 ? ((it >> 1) & 1) : (it & 1);
         const C* tile = reinterpret_cast<const C*>(smtma + (size_t)sl * slot_bytes);   // [box][c][y][kx]
-        const bool ok = mbar_wait_bounded(&bar[sl], (it >> 1) & 1);
+        const bool ok = mbar_wait_bounded(&bar[sl], par);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicExch(d.err, kErrTmaTimeout);
-                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((it + 1) >> 1) & 1);
+                if (NSLOT == 2 && t + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(&bar[sl ^ 1], ((it + 1) >> 1) & 1);
             }
             return;
         }
@@ -361,9 +369,9 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             if (k > 0 && 2 * k < LX) work[(LX - k) * LS + l] = mk<C>(A.x + Bv.y, Bv.x - A.y);
         }
         __syncthreads();   // slot consumed
-        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+        if (tid == 0 && t + NSLOT * (int)gridDim.x < ntiles) {
             fence_proxy_async_smem();
-            issue(t + 2 * gridDim.x, sl);
+            issue(t + NSLOT * gridDim.x, sl);
         }
         {
             C v[FI::NR];
@@ -585,6 +593,8 @@ p_y_tma(DemagDims d, const __grid_constant__ CUtensorMap in_map, typename Cplx<T
         fence_mbar_init();
     }
     __syncthreads();
+    grid_dep_launch();
+    grid_dep_wait();      // the previous pass's output is complete from here on
     auto issue = [&](int t, int sl) {
         const int kt = t % nkt, cz = t / nkt;
         C* dst = sl ? slot1 : slot0;
@@ -855,6 +865,8 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
         fence_mbar_init();
     }
     __syncthreads();
+    grid_dep_launch();
+    grid_dep_wait();      // the previous pass's output is complete from here on
     auto ky_of = [&](int kyo, int& p, int& side) {
         p = (kyo + 1) >> 1;
         side = (kyo > 0 && (kyo & 1) == 0) ? 1 : 0;
@@ -1082,6 +1094,24 @@ template <typename K> static int persistent_grid(K kernel, int threads, size_t s
     return work < g ? work : g;
 }
 
+// launch with programmatic stream serialization (the kernel calls
+// grid_dep_wait before it reads what the previous kernel wrote)
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // TMA y pass (FP32 only): returns false if it could not be used (caller falls back)
 // kx columns per TMA tile: two slots of L x B complex floats stay within 128 KB
 template <int L> constexpr int b_tma() { return (4096 / L) < 8 ? ((4096 / L) < 2 ? 2 : 4096 / L) : 8; }
@@ -1106,7 +1136,7 @@ static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cud
     set_smem(k, sm);
     const int nkt = (d.KX + B - 1) / B;
     const int grid = persistent_grid(k, threads, sm, nkt * 3 * d.nz);
-    k<<<grid, threads, sm, st>>>(d, map, out, box_rows, nboxes);
+    launch_pdl(k, grid, threads, sm, st, d, map, out, box_rows, nboxes);
     return true;
 }
 
@@ -1147,7 +1177,7 @@ static bool launch_p3_tma(const DemagDims& d, float2* S2, const float* tens, cud
     const int threads = B * Fft<float, L, -1, (L > 1)>::TPL;
     const int nkt = (d.KX + B - 1) / B;
     const int grid = persistent_grid(k, threads, sm, nkt * d.LY);
-    k<<<grid, threads, sm, st>>>(d, s2m, tm, S2, slot_bytes, s2_area);
+    launch_pdl(k, grid, threads, sm, st, d, s2m, tm, S2, slot_bytes, s2_area);
     return true;
 }
 
@@ -1266,8 +1296,11 @@ template <typename T, int L> static void launch_x_inv(const DemagDims& d, const 
 }
 
 // fused K5 launcher (see k5_fused): false if the shape or material does not qualify
+// k5_fused configuration: TMA slots, work-area row padding, resident CTAs per SM
+constexpr int kK5Rows = 2, kK5Slots = 1, kK5Pad = 0, kK5MinBlocks = 8;
+
 template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st) {
-    constexpr int TY = 4;
+    constexpr int TY = kK5Rows;
     if constexpr (L < 16) {
         return false;
     } else {
@@ -1286,15 +1319,15 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         if (!encode_4d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, S1, dims, strides, box)) return false;
         constexpr int NL = 3 * TY / 2;
         const int slot_bytes = (int)(((size_t)nb * w * TY * 3 * sizeof(float2) + 127) / 128 * 128);
-        const size_t sm = 2 * (size_t)slot_bytes + (size_t)L * (NL + 1) * sizeof(float2) + 16;
+        const size_t sm = kK5Slots * (size_t)slot_bytes + (size_t)L * (NL + kK5Pad) * sizeof(float2) + 16;
         if (sm > 220 * 1024) return false;
-        auto k = k5_fused<L, TY>;
+        auto k = k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks>;
         set_smem(k, sm);
         const int threads = NL * Fft<float, L, +1, false>::TPL;
         if (threads > 1024) return false;
         const int ntiles = ((d.ny + TY - 1) / TY) * d.nz;
         const int grid = persistent_grid(k, threads, sm, ntiles);
-        k<<<grid, threads, sm, st>>>(d, map, S1, p, w, nb, slot_bytes);
+        launch_pdl(k, grid, threads, sm, st, d, map, S1, p, w, nb, slot_bytes);
         return true;
     }
 }
@@ -1380,7 +1413,7 @@ bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cu
 bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
     if (!d.err || d.LX < 16 || d.LX > 4096 || d.nx % 2 != 0) return false;
     if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.Ms == 0.f) return false;
-    const int threads = 6 * (d.LX / 16);
+    const int threads = (3 * kK5Rows / 2) * (d.LX / 16);
     return threads <= 1024;
 }
 
