@@ -836,15 +836,23 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
 // Persistent TMA variant of the register-resident z pass (FP32, Pz <= 256):
 // tile = (16 kx columns, one ky); tiles run ky = 0, 1, Py-1, 2, Py-2, ... so
 // that the two wave numbers sharing a tensor slice are neighbours in time.
-// Each slot holds the tile's three z-columns (TMA box 16 x 1 x nz x 3 of S2)
-// and its tensor slice (box 16 x 1 x (Pz/2+1) x 6); the S2 part doubles as
-// the transforms' exchange scratch once the registers are loaded.
+// Shared memory holds one tile's three z-columns (TMA box 16 x 1 x nz x 3 of
+// S2), one tensor slice (box 16 x 1 x (Pz/2+1) x 6) and the transforms'
+// exchange scratch.  The two loads complete on separate barriers and are
+// single-buffered: the next tile's columns are requested as soon as this
+// tile's are in registers, its tensor slice once the multiply has read this
+// one, so each load has a whole transform to land in while three CTAs share
+// an SM.
+template <int LZ, int B> constexpr int p3_min_blocks_tma() {
+    return (384 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL)) < 1 ? 1
+           : (384 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL)) > 8 ? 8
+           : 384 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL);
+}
+
 template <int LZ, int B>
-__global__ void __launch_bounds__(B * Fft<float, LZ, -1, (LZ > 1)>::TPL,
-                                  (256 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL)) > 1
-                                      ? 256 / (B * Fft<float, LZ, -1, (LZ > 1)>::TPL) : 1)
+__global__ void __launch_bounds__(B * Fft<float, LZ, -1, (LZ > 1)>::TPL, (p3_min_blocks_tma<LZ, B>()))
 p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_constant__ CUtensorMap t_map,
-         float2* __restrict__ S2, int slot_bytes, int s2_bytes) {
+         float2* __restrict__ S2, int s2_bytes, int t_bytes) {
     using C = float2;
     using FF = Fft<float, LZ, -1, (LZ > 1)>;
     using FI = Fft<float, LZ, +1, false>;
@@ -852,16 +860,20 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
     constexpr int NOUT = LZ == 1 ? 1 : NR / 2;
     constexpr int KZ2 = LZ / 2 + 1;
     extern __shared__ __align__(128) unsigned char smtma[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + 2 * (size_t)slot_bytes);
+    C* cs = reinterpret_cast<C*>(smtma);                                        // [c][z][kx]
+    const float* ts = reinterpret_cast<const float*>(smtma + s2_bytes);         // [comp][kz'][kx]
+    C* scr = reinterpret_cast<C*>(smtma + s2_bytes + t_bytes);                  // [LZ][kx]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + s2_bytes + t_bytes + (size_t)LZ * B * sizeof(C));
     const int tid = threadIdx.x;
     const int line = tid % B, j = tid / B;
     const int nz = d.nz, LY = d.LY;
     const int nkt = (d.KX + B - 1) / B;
     const int ntiles = nkt * LY;
-    const uint32_t tx_bytes = (uint32_t)(3 * nz * B * sizeof(C) + 6 * KZ2 * B * sizeof(float));
+    const uint32_t s2_tx = (uint32_t)(3 * nz * B * sizeof(C));
+    const uint32_t t_tx = (uint32_t)(6 * KZ2 * B * sizeof(float));
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar[0], 1);     // S2 columns
+        mbar_init(&bar[1], 1);     // tensor slice
         fence_mbar_init();
     }
     __syncthreads();
@@ -872,31 +884,35 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
         side = (kyo > 0 && (kyo & 1) == 0) ? 1 : 0;
         return side ? LY - p : p;
     };
-    auto issue = [&](int t, int sl) {
+    auto issue_s2 = [&](int t) {
         const int kt = t % nkt, kyo = t / nkt;
         int p, side;
         const int ky = ky_of(kyo, p, side);
-        unsigned char* base = smtma + (size_t)sl * slot_bytes;
-        mbar_arrive_expect_tx(&bar[sl], tx_bytes);
-        tma_load_4d(base, &s2_map, &bar[sl], kt * B, ky, 0, 0);
-        tma_load_4d(base + s2_bytes, &t_map, &bar[sl], kt * B, p, 0, 0);
+        mbar_arrive_expect_tx(&bar[0], s2_tx);
+        tma_load_4d(smtma, &s2_map, &bar[0], kt * B, ky, 0, 0);
+    };
+    auto issue_t = [&](int t) {
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        ky_of(kyo, p, side);
+        mbar_arrive_expect_tx(&bar[1], t_tx);
+        tma_load_4d(smtma + s2_bytes, &t_map, &bar[1], kt * B, p, 0, 0);
     };
     const int t0 = blockIdx.x;
-    if (tid == 0) {
-        if (t0 < ntiles) issue(t0, 0);
-        if (t0 + (int)gridDim.x < ntiles) issue(t0 + gridDim.x, 1);
+    if (tid == 0 && t0 < ntiles) {
+        issue_s2(t0);
+        issue_t(t0);
     }
     int i = 0;
     for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
-        const int sl = i & 1;
-        unsigned char* base = smtma + (size_t)sl * slot_bytes;
-        C* cs = reinterpret_cast<C*>(base);                       // [c][z][kx]
-        const float* ts = reinterpret_cast<const float*>(base + s2_bytes);   // [comp][kz'][kx]
-        const bool ok = mbar_wait_bounded(&bar[sl], (i >> 1) & 1);
+        const uint32_t par = i & 1;
+        const bool more = t + (int)gridDim.x < ntiles;
+        bool ok = mbar_wait_bounded(&bar[0], par);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicExch(d.err, kErrTmaTimeout);
-                if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[sl ^ 1], ((i + 1) >> 1) & 1);
+                mbar_wait_bounded(&bar[0], par);                 // the late columns
+                mbar_wait_bounded(&bar[1], par);                 // this tile's tensor slice is in flight
             }
             return;
         }
@@ -912,9 +928,23 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
             vy[r] = live ? cs[(1 * nz + z) * B + line] : mk<C>(0, 0);
             vz[r] = live ? cs[(2 * nz + z) * B + line] : mk<C>(0, 0);
         }
-        FF::run(vx, cs + line, B, j);
-        FF::run(vy, cs + line, B, j);
-        FF::run(vz, cs + line, B, j);
+        __syncthreads();   // the columns are in registers: the buffer takes the next tile's
+        if (tid == 0 && more) {
+            fence_proxy_async_smem();
+            issue_s2(t + gridDim.x);
+        }
+        FF::run(vx, scr + line, B, j);
+        FF::run(vy, scr + line, B, j);
+        FF::run(vz, scr + line, B, j);
+        ok = mbar_wait_bounded(&bar[1], par);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                mbar_wait_bounded(&bar[1], par);                  // the late slice
+                if (more) mbar_wait_bounded(&bar[0], par ^ 1u);   // the next tile's columns are in flight
+            }
+            return;
+        }
         const float sy = side ? -1.f : 1.f;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -932,9 +962,14 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
             vy[r] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
             vz[r] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
         }
-        FI::run(vx, cs + line, B, j);
-        FI::run(vy, cs + line, B, j);
-        FI::run(vz, cs + line, B, j);
+        __syncthreads();   // the slice has been read: the buffer takes the next tile's
+        if (tid == 0 && more) {
+            fence_proxy_async_smem();
+            issue_t(t + gridDim.x);
+        }
+        FI::run(vx, scr + line, B, j);
+        FI::run(vy, scr + line, B, j);
+        FI::run(vz, scr + line, B, j);
         const int kx = kt * B + line;
         if (kx < d.KX) {
             const long cstride = (long)nz * LY * d.KXS, zs = (long)LY * d.KXS;
@@ -948,11 +983,6 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
                     col[2 * cstride + z * zs] = vz[r];
                 }
             }
-        }
-        __syncthreads();   // every thread is done with this slot
-        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
-            fence_proxy_async_smem();
-            issue(t + 2 * gridDim.x, sl);
         }
     }
 }
@@ -1168,16 +1198,14 @@ static bool launch_p3_tma(const DemagDims& d, float2* S2, const float* tens, cud
     if (!encode_4d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tens, td, ts, tb)) return false;
     const int s2_bytes = (int)((3 * (size_t)d.nz * B * sizeof(float2) + 127) / 128 * 128);
     const int t_bytes = (int)((6 * (size_t)KZ2 * B * sizeof(float) + 127) / 128 * 128);
-    // the S2 part of a slot is also the transforms' scratch: L x B complex values
-    const int s2_area = s2_bytes > (int)(L * B * sizeof(float2)) ? s2_bytes : (int)(L * B * sizeof(float2));
-    const int slot_bytes = s2_area + t_bytes;
-    const size_t sm = 2 * (size_t)slot_bytes + 16;
+    const size_t sm = (size_t)s2_bytes + t_bytes + (size_t)L * B * sizeof(float2) + 16;
+    if (sm > 220 * 1024) return false;
     auto k = p3_z_tma<L, B>;
     set_smem(k, sm);
     const int threads = B * Fft<float, L, -1, (L > 1)>::TPL;
     const int nkt = (d.KX + B - 1) / B;
     const int grid = persistent_grid(k, threads, sm, nkt * d.LY);
-    launch_pdl(k, grid, threads, sm, st, d, s2m, tm, S2, slot_bytes, s2_area);
+    launch_pdl(k, grid, threads, sm, st, d, s2m, tm, S2, s2_bytes, t_bytes);
     return true;
 }
 
