@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -88,6 +90,18 @@ def model_stage_bytes(n, s):
     tens = 6 * s * KX * (ny + 1) * (nz + 1)
     local = (73.0 / 4.0) * s * nx * ny * nz
     return fft + tens + local
+
+
+def floor_stage_bytes(n, s):
+    """Compulsory traffic of one stage with no intermediates: m_s read once,
+    the tensor spectrum once, and the RK state (m_n, acc read/write, grain id,
+    m_{s+1} write)."""
+    nx, ny, nz = n
+    LX, LY, LZ = padded(n)
+    KX = LX // 2 + 1
+    N = nx * ny * nz
+    tens = 6 * s * KX * (ny + 1) * (nz + 1)
+    return tens + N * (3 * s + 1 + 3 * s + 2 * (3 * s) * 0.75 + 3 * s)
 
 
 def stage_flops(n):
@@ -284,6 +298,89 @@ def e2e_measure(torch, s, w, steps, warmup):
     return el, nbytes
 
 
+def b1_cufft_measure(torch, w, steps, warmup, s32):
+    """Comparison baseline B1: the same RK4 stage written as library FFTs and
+    separate elementwise PyTorch kernels -- torch.fft (cuFFT) rfftn/irfftn over
+    the full zero-padded grid, the 3x3 multiply with the unfolded real tensor
+    spectrum, the exchange stencil by slicing, anisotropy, LLG and the RK4
+    combination as tensor expressions.  FP32, inputs resident, timed with CUDA
+    events like the main path.  Also returns its field's relative max-norm
+    difference from mm_heff's FP32 field on the same m."""
+    from paper_2302_08843_gb300.binding import demag_spectrum_host, padded_extents
+    from paper_2302_08843_gb300.workloads import to_soa
+    mu0, gamma = 4e-7 * math.pi, 2.21e5
+    dev = "cuda"
+    nx, ny, nz = w.n
+    Px, Py, Pz = padded_extents(w.n)
+    oct_ = torch.from_numpy(demag_spectrum_host(w.n, w.dx)).float().to(dev)     # [6][Pz/2+1][Py/2+1][Kx]
+    kz = torch.arange(Pz, device=dev)
+    ky = torch.arange(Py, device=dev)
+    kzf = torch.minimum(kz, Pz - kz) if Pz > 1 else kz
+    kyf = torch.minimum(ky, Py - ky) if Py > 1 else ky
+    sz = torch.where(2 * kz <= Pz, 1.0, -1.0).to(dev)[:, None, None]
+    sy = torch.where(2 * ky <= Py, 1.0, -1.0).to(dev)[None, :, None]
+    full = oct_[:, kzf][:, :, kyf]                                                # [6][Pz][Py][Kx]
+    Nxx, Nxy, Nxz, Nyy, Nyz, Nzz = full[0], full[1] * sy, full[2] * sz, full[3], full[4] * sy * sz, full[5]
+    del oct_, full
+    Ms, A, Ku, al = float(w.Ms), float(w.A), float(w.Ku1), float(w.alpha)
+    axes = torch.from_numpy(to_soa(w.ku_axis_cells().astype(np.float32))).to(dev)   # [3][nz][ny][nx]
+    cex = 2.0 * A / (mu0 * Ms)
+    cani = 2.0 * Ku / (mu0 * Ms)
+    gp = -gamma / (1.0 + al * al)
+    idx2 = [1.0 / (d * d) for d in w.dx]
+
+    def heff(m):
+        Mp = torch.zeros((3, Pz, Py, Px), device=dev, dtype=torch.float32)
+        Mp[:, :nz, :ny, :nx] = Ms * m
+        Mh = torch.fft.rfftn(Mp, dim=(1, 2, 3))
+        hx = Nxx * Mh[0] + Nxy * Mh[1] + Nxz * Mh[2]
+        hy = Nxy * Mh[0] + Nyy * Mh[1] + Nyz * Mh[2]
+        hz = Nxz * Mh[0] + Nyz * Mh[1] + Nzz * Mh[2]
+        h = torch.fft.irfftn(torch.stack((hx, hy, hz)), s=(Pz, Py, Px), dim=(1, 2, 3), norm="forward")
+        h = h[:, :nz, :ny, :nx].contiguous()
+        mp = torch.nn.functional.pad(m[None], (1, 1, 1, 1, 1, 1), mode="replicate")[0]
+        lap = (idx2[0] * (mp[:, 1:-1, 1:-1, 2:] + mp[:, 1:-1, 1:-1, :-2] - 2 * m)
+               + idx2[1] * (mp[:, 1:-1, 2:, 1:-1] + mp[:, 1:-1, :-2, 1:-1] - 2 * m)
+               + idx2[2] * (mp[:, 2:, 1:-1, 1:-1] + mp[:, :-2, 1:-1, 1:-1] - 2 * m))
+        h = h + cex * lap + cani * (axes * m).sum(0, keepdim=True) * axes
+        return h
+
+    def rhs(m):
+        h = heff(m)
+        c = torch.cross(m, h, dim=0)
+        return gp * (c + al * torch.cross(m, c, dim=0))
+
+    def rk4(m, dt):
+        k1 = rhs(m)
+        k2 = rhs(m + 0.5 * dt * k1)
+        k3 = rhs(m + 0.5 * dt * k2)
+        k4 = rhs(m + dt * k3)
+        y = m + (dt / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+        return y / torch.linalg.vector_norm(y, dim=0, keepdim=True)
+
+    m = torch.from_numpy(to_soa(w.m0.astype(np.float32))).to(dev)
+    h_ours = s32.heff(m).double()
+    h_b1 = heff(m).double()
+    diff = float((h_b1 - h_ours).abs().max() / h_ours.abs().max())
+    for _ in range(warmup):
+        m = rk4(m, w.dt)
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        m = rk4(m, w.dt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"value": w.ncells * STAGES_PER_STEP * steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_stage": round(ms / steps / STAGES_PER_STEP, 4), "steps": steps,
+            "field_rel_diff_vs_libmm_fp32": diff,
+            "what": "torch.fft rfftn/irfftn (cuFFT) over the full padded grid + separate elementwise "
+                    "PyTorch kernels, FP32"}
+
+
 def serve_measure(torch, n_requests):
     """The served stream (Poisson arrivals, mean 2 ms; five grid shapes; FP32
     batched relax under a 40 GB footprint cap): p50/p99 latency and
@@ -395,10 +492,14 @@ def run_ours(args):
             clocks = sampler.stop(set(idx[:ws]))
         ms_max = allmax(ms)
         el_e2e = nbytes = None
+        b1 = None
         if precision == "fp32":
             el_e2e, nbytes = e2e_measure(torch, s, w, max(3, steps // 5), 2)
             el_e2e = allmax(el_e2e)
-        results[precision] = dict(ms=ms_max, steps=steps, prof=prof, e2e=(el_e2e, nbytes, max(3, steps // 5)))
+            if not args.nz and not args.no_b1:
+                b1 = b1_cufft_measure(torch, w, max(3, steps // 5), 2, s)
+                torch.cuda.empty_cache()
+        results[precision] = dict(ms=ms_max, steps=steps, prof=prof, e2e=(el_e2e, nbytes, max(3, steps // 5)), b1=b1)
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -445,9 +546,12 @@ def run_ours(args):
     model_b = model_stage_bytes(w.n, 4)
     ach_stage = model_b / (stage_ms / 1e3) / 1e9
     kern_sum = sum(kernel_bytes(w.n, 4).values()) * 1.0
+    floor_b = floor_stage_bytes(w.n, 4)
     stage_roof = {"model_bytes_per_stage": int(model_b), "ms_per_stage": round(stage_ms, 4),
                   "achieved_gbs": round(ach_stage, 1), "frac": round(ach_stage / hbm_peak, 4),
-                  "kernel_bytes_per_stage": int(kern_sum)}
+                  "kernel_bytes_per_stage": int(kern_sum),
+                  "floor_bytes_per_stage": int(floor_b),
+                  "frac_of_floor": round(floor_b / (stage_ms / 1e3) / 1e9 / hbm_peak, 4)}
     if args.nz:
         print(json.dumps({"profiling_case": "bulk cropped to %dx%dx%d" % tuple(w.n), "value": value,
                           "kernels": kernels32}))
@@ -475,6 +579,8 @@ def run_ours(args):
                       "l2": "per-stage working set ~0.7 GB > 129 MB L2, no flush"},
            "roofline": roof, "stage_roofline": stage_roof, "kernels": kernels32,
            "gpu_launches": launches, "e2e": e2e, "fp64": fp64, "clocks": clocks}
+    if r32.get("b1"):
+        out["b1_cufft"] = dict(r32["b1"], ours_over_b1=round(value / r32["b1"]["value"], 3))
     if args.serve_requests > 0 and ws == 1:
         out["serving"] = serve_measure(torch, args.serve_requests)
     if cpu is not None:
@@ -534,6 +640,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-b1", action="store_true", help="skip the cuFFT + elementwise comparison baseline")
     ap.add_argument("--nz", type=int, default=0,
                     help="profiling case: the bulk workload cropped to nz planes (the printed line is not a bench "
                          "result)")
