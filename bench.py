@@ -220,6 +220,33 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(torch, dist, v, device):
+    """The largest of every rank's v (all ranks get it); v itself without a
+    process group."""
+    if dist is None:
+        return v
+    tt = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def serve_replicas(torch, dist, rank, ws, requests, server):
+    """Replicas only: rank r serves requests r, r+ws, ... of the stream with
+    its own server (no collective on the data path); rank 0 gathers every
+    result and the max elapsed time.  Returns (results in stream order,
+    elapsed) on rank 0 and (None, elapsed) elsewhere."""
+    from paper_2302_08843_gb300.serving import shard, unshard
+    mine = shard(requests, rank, ws)
+    res = server.run(mine, realtime=True)
+    elapsed = max_over_ranks(torch, dist, server.elapsed, "cpu" if dist is None or
+                             dist.get_backend() == "gloo" else "cuda")
+    if dist is None:
+        return res, elapsed
+    parts = [None] * ws if rank == 0 else None
+    dist.gather_object(res, parts, dst=0)
+    return (unshard(parts, len(requests)) if rank == 0 else None), elapsed
+
+
 def traffic_for(kernel, precision):
     """ncu DRAM bytes per launch from the committed profile summary, or None
     when the kernel sources changed since the counters were taken."""
@@ -381,7 +408,7 @@ def b1_cufft_measure(torch, w, steps, warmup, s32):
                     "PyTorch kernels, FP32"}
 
 
-def serve_measure(torch, n_requests):
+def serve_measure(torch, n_requests, dist=None, rank=0, ws=1):
     """The served stream (Poisson arrivals, mean 2 ms; five grid shapes; FP32
     batched relax under a 40 GB footprint cap): p50/p99 latency and
     throughput of its first n_requests requests, next to the plain per-solve
@@ -395,14 +422,19 @@ def serve_measure(torch, n_requests):
     stream = W.serving_stream()
     reqs = stream[:n_requests]
     srv = Server(precision="fp32", hbm_cap=40e9)
-    res = srv.run(reqs, realtime=True)
-    summ = latency_summary(res, srv.elapsed)
-    cell_steps = sum(w.ncells * r["steps"] for (_, w), r in zip(reqs, res))
-    summ.update({"elapsed_s": round(srv.elapsed, 3), "graph_launches": srv.launches,
-                 "cell_steps_per_s": cell_steps / srv.elapsed, "peak_footprint_bytes": int(srv.peak_used),
-                 "sample": "first %d of the 512-request stream (arrivals as drawn)" % len(reqs)})
+    res, elapsed = serve_replicas(torch, dist, rank, ws, reqs, srv)
+    launches, peak = srv.launches, srv.peak_used
     srv.close()
     torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+    summ = latency_summary(res, elapsed)
+    cell_steps = sum(w.ncells * r["steps"] for (_, w), r in zip(reqs, res))
+    summ.update({"elapsed_s": round(elapsed, 3), "graph_launches_rank0": launches,
+                 "cell_steps_per_s": cell_steps / elapsed, "peak_footprint_bytes_rank0": int(peak),
+                 "replicas": ws,
+                 "sample": "first %d of the 512-request stream (arrivals as drawn)%s" %
+                           (len(reqs), "" if ws == 1 else ", request i served by rank i mod %d" % ws)})
     per = {}
     ferr = {}
     shapes = []
@@ -468,11 +500,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def allmax(v):
-        if dist is None:
-            return v
-        tt = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return max_over_ranks(torch, dist, v, "cuda")
 
     results = {}
     clocks = None
@@ -504,6 +532,9 @@ def run_ours(args):
         del s
         torch.cuda.empty_cache()
 
+    serving = None
+    if args.serve_requests > 0 and not args.nz:
+        serving = serve_measure(torch, args.serve_requests, dist, rank, ws)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -581,8 +612,8 @@ def run_ours(args):
            "gpu_launches": launches, "e2e": e2e, "fp64": fp64, "clocks": clocks}
     if r32.get("b1"):
         out["b1_cufft"] = dict(r32["b1"], ours_over_b1=round(value / r32["b1"]["value"], 3))
-    if args.serve_requests > 0 and ws == 1:
-        out["serving"] = serve_measure(torch, args.serve_requests)
+    if serving is not None:
+        out["serving"] = serving
     if cpu is not None:
         out["cpu_baseline"] = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stage of the FP64 oracle on the "
                                                   "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")

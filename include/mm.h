@@ -135,7 +135,10 @@ mm_status mm_demag_disable(mm_state* s);
  * receives (E_demag, E_exchange, E_anisotropy, E_zeeman) in joules
  * (Eq. linear_energy_discrete for the first three, -mu0 V sum Ms m.h for
  * Zeeman); asking for E_out synchronises the stream.  torque_out: host double
- * or NULL, receives max over cells of |m x h| / Ms (synchronises). */
+ * or NULL, receives max over cells of |m x h| / Ms (synchronises).  When
+ * E_out or torque_out is asked for and a cell's field or torque is not
+ * finite, the call returns MM_ENONFINITE (h_out and the scalars are still
+ * written). */
 mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], double t,
                   double* torque_out);
 
@@ -231,6 +234,17 @@ mm_status mm_batch_end(mm_batch* b, int* status, int* steps, double* torque);
 
 /* Copy a slot's magnetisation out (host copies synchronise). */
 mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
+
+/* Diagnostic (the paper has no counterpart): enqueue on the state's stream
+ * one CTA that waits on an mbarrier nothing ever completes, polling it at most
+ * `spins` times the way the TMA kernels wait for their copies.  When the
+ * budget runs out the kernel writes the timeout code into the state's device
+ * error word and returns, as a kernel whose copy never landed would; the next
+ * call that reads results from this state (mm_heff with energies or torque,
+ * a DP45 step, mm_relax) then returns MM_ETIMEOUT, and so does every later
+ * one: destroy the state.  The GPU context stays usable.  MM_EINVAL if
+ * spins < 1. */
+mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins);
 
 /* Host-only helper (no GPU): the real-space demag tensor this library builds
  * (Sec. 4.4, same rule as mm_demag_setup) for every cell offset, as

@@ -26,7 +26,8 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
-           "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m")
+           "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
+           "mm_selftest_wait_timeout")
 
 
 class MMError(RuntimeError):
@@ -93,6 +94,7 @@ def lib():
         "mm_batch_clear_slot": (i, [vp, i]),
         "mm_batch_begin": (i, [vp, i, d, d, i]),
         "mm_batch_query": (i, [vp, vp]),
+        "mm_selftest_wait_timeout": (i, [vp, ctypes.c_uint]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -285,6 +287,10 @@ class State:
         if torque:
             out.append(tq.value)
         return out[0] if len(out) == 1 else tuple(out)
+
+    def selftest_wait_timeout(self, spins=1 << 16):
+        """mm_selftest_wait_timeout: a device wait that runs out on this state's stream."""
+        check(lib().mm_selftest_wait_timeout(self.h, int(spins)))
 
     def step(self, dt, t=0.0, method="rk4", rtol=1e-5):
         """One mm_llg_step; returns (t_new, dt_next)."""

@@ -46,6 +46,9 @@ template <typename T>
 void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
                  typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm);
 
+// diagnostic: one CTA whose bounded wait on a never-completed mbarrier runs out
+void launch_diag_wait(int* err, unsigned spins, cudaStream_t st);
+
 template <typename T> struct AdjParams;
 template <typename T> void launch_adj_prep(const AdjParams<T>& p, cudaStream_t st);
 template <typename T> void launch_adj_finish(const AdjParams<T>& p, cudaStream_t st);

@@ -335,6 +335,7 @@ mm_status heff_impl(mm_state* s, const void* m, void* h_out, double* E_out, doub
         if (E_out)
             for (int q = 0; q < 4; ++q) E_out[q] = s->h_scalars[R_EDEM + q];
         if (torque_out) *torque_out = s->h_scalars[R_TORQUE];
+        if (s->h_scalars[R_NONFINITE] != 0.0) return fail(MM_ENONFINITE, "non-finite field or torque");
     }
     return MM_OK;
 }
@@ -1069,6 +1070,15 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)
                               : adjoint_impl<float>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t);
+}
+
+mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins) {
+    MM_TRY(check_state(s));
+    MM_TRY(set_device(s));
+    if (spins < 1) return fail(MM_EINVAL, "spins must be >= 1");
+    launch_diag_wait(s->dev_err, spins, s->st);
+    MM_LAUNCHED();
+    return MM_OK;
 }
 
 size_t mm_batch_footprint(const mm_grid* grid, mm_precision precision, int capacity) {

@@ -189,6 +189,22 @@ class Server:
         self.used = 0
 
 
+def shard(requests, rank, world):
+    """Requests rank, rank + world, ... of a stream (arrival times kept): the
+    stream's share of one replica when each GPU runs its own server."""
+    return [requests[i] for i in range(rank, len(requests), world)]
+
+
+def unshard(parts, count):
+    """Inverse of shard: per-rank result lists back in stream order."""
+    world = len(parts)
+    out = [None] * count
+    for r, part in enumerate(parts):
+        for k, res in enumerate(part):
+            out[r + k * world] = res
+    return out
+
+
 def latency_summary(results, elapsed):
     """p50/p99/mean latency (arrival -> result, s) and throughput of served requests."""
     done = [r for r in results if r["status"] != Server.REJECTED]
