@@ -263,13 +263,17 @@ def traffic_for(kernel, precision):
     return None if e is None else e.get("dram_bytes_per_launch")
 
 
+# the files that define the timed FP32 stage kernels (device code and the
+# launch configuration); a change to any of them invalidates stored counters
+KERNEL_SOURCES = ("demag_passes.cu", "fft_engine.cuh", "common.cuh", "tma.cuh", "demag.h")
+
+
 def source_hash():
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2302_08843_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            h.update(open(os.path.join(src, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
 
