@@ -9,7 +9,10 @@ Problem  : one micromagnetic problem (grid, material, field terms); evaluates
 rk4_step : classic fourth-order Runge-Kutta (Sec. 3: explicit RK methods).
 dp45_*   : Dormand-Prince 5(4) with first-same-as-last and an embedded
            fourth-order error estimate (the adaptive explicit RK family of
-           Sec. 3; the paper's default is RKF45).
+           Sec. 3).
+rkf45_*  : Runge-Kutta-Fehlberg 4(5), the paper's default solver (Sec. 3):
+           the fourth-order solution is propagated, the fifth-order one only
+           controls the error.
 relax    : integrate with the material's damping until the maximum torque is
            small (Sec. 3, ground state by integrating the LLG).
 
@@ -22,6 +25,13 @@ Readings where the paper is silent:
   renormalisation, is the first stage of the next step.
 * Relaxation stops when max_i |y5_i x h(y5)_i| / Ms_i < tol, read from the
   field of that last stage (no extra field evaluation).
+* RKF45 uses the same error norm with the propagated (fourth-order) solution
+  in place of y5, the same accept rule and the same step-size factor; it has
+  no first-same-as-last stage, so the torque that stops a relaxation is read
+  from the first stage of the next step (the field at the new m).
+* "Without the precession term" (Sec. 3, ground states): the m x h term of
+  Eq. llg is dropped and the damping term keeps its factor
+  gamma alpha / (1 + alpha^2).
 """
 import numpy as np
 
@@ -32,11 +42,13 @@ from .fields import (anisotropy_field, exchange_field, linear_energy,
 from .newell import demag_tensor
 
 
-def llg_rhs(m, h, alpha):
-    """Eq. llg with the reduced gyromagnetic ratio gamma = 2.21e5 m/(A s)."""
+def llg_rhs(m, h, alpha, precession=True):
+    """Eq. llg with the reduced gyromagnetic ratio gamma = 2.21e5 m/(A s);
+    without the precession term the m x h summand is left out."""
     alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), m.shape[:3])[..., None]
     mxh = np.cross(m, h)
-    return -GAMMA / (1.0 + alpha * alpha) * (mxh + alpha * np.cross(m, mxh))
+    damp = alpha * np.cross(m, mxh)
+    return -GAMMA / (1.0 + alpha * alpha) * ((mxh + damp) if precession else damp)
 
 
 class Problem:
@@ -47,7 +59,7 @@ class Problem:
     (nx, ny, nz) multiplier of the external field; p: Newell radius."""
 
     def __init__(self, n, dx, Ms, A, alpha, Ku1=0.0, ku_axis=(1.0, 0.0, 0.0),
-                 h_ext=(0.0, 0.0, 0.0), h_ext_weight=None, p=20, demag=True, Nt=None):
+                 h_ext=(0.0, 0.0, 0.0), h_ext_weight=None, p=20, demag=True, Nt=None, precession=True):
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
         self.V = self.dx[0] * self.dx[1] * self.dx[2]
@@ -59,6 +71,7 @@ class Problem:
         self.h_ext = h_ext
         self.h_ext_weight = h_ext_weight
         self.demag = demag
+        self.precession = precession
         if demag:
             self.Nt = demag_tensor(self.n, self.dx, p) if Nt is None else Nt
             self.Nhat = tensor_spectrum(self.Nt, self.n)
@@ -96,7 +109,7 @@ class Problem:
                 zeeman_energy(m, terms["zeeman"], self.Ms, self.V))
 
     def rhs(self, m, t):
-        return llg_rhs(m, self.heff(m, t), self.alpha)
+        return llg_rhs(m, self.heff(m, t), self.alpha, self.precession)
 
     def max_torque(self, m, h):
         """max_i |m_i x h_i| / Ms_i over cells with Ms_i != 0."""
@@ -156,7 +169,7 @@ def dp45_attempt(prob, m, t, dt, k1, rtol, atol=None):
             if a != 0.0:
                 y = y + dt * a * ks[j]
         h = prob.heff(y, t + DP_C[s] * dt)
-        ks.append(llg_rhs(y, h, prob.alpha))
+        ks.append(llg_rhs(y, h, prob.alpha, prob.precession))
         if s == 6:
             y5, h7 = y, h
     e = np.zeros_like(m)
@@ -198,13 +211,73 @@ def dp45_integrate(prob, m, t0, t1, dt0=1e-13, rtol=1e-5, atol=None, renorm=True
     return m, t, dt, acc, rej
 
 
-def relax(prob, m, tol=1e-3, max_steps=20000, dt0=1e-13, rtol=1e-5, atol=None, renorm=True, t0=0.0):
-    """Integrate with DP45 until max |m x h| / Ms < tol (or max_steps accepted
-    steps).  Returns (m, steps, max_torque, t)."""
+# Runge-Kutta-Fehlberg 4(5) tableau (E. Fehlberg, NASA TR R-315, 1969)
+RKF_C = (0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0)
+RKF_A = (
+    (),
+    (1.0 / 4.0,),
+    (3.0 / 32.0, 9.0 / 32.0),
+    (1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0),
+    (439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0),
+    (-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0),
+)
+RKF_B4 = (25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0)
+RKF_B5 = (16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0)
+
+
+def rkf45_attempt(prob, m, t, dt, k1, rtol, atol=None):
+    """One Fehlberg attempt from (m, t) with step dt and first stage k1 = f(m, t).
+
+    Returns (y4, err): the fourth-order solution (not renormalised) and the
+    error norm of its difference to the fifth-order one."""
+    atol = rtol if atol is None else atol
+    ks = [k1]
+    for s in range(1, 6):
+        y = m.copy()
+        for j, a in enumerate(RKF_A[s]):
+            if a != 0.0:
+                y = y + dt * a * ks[j]
+        ks.append(prob.rhs(y, t + RKF_C[s] * dt))
+    y4 = m.copy()
+    e = np.zeros_like(m)
+    for j in range(6):
+        y4 = y4 + dt * RKF_B4[j] * ks[j]
+        e = e + dt * (RKF_B5[j] - RKF_B4[j]) * ks[j]
+    sc = atol + rtol * np.maximum(np.abs(m), np.abs(y4))
+    return y4, float(np.max(np.abs(e) / sc))
+
+
+def rkf45_step(prob, m, t, dt, rtol=1e-5, atol=None, renorm=True, k1=None):
+    """Attempts from (m, t) until one is accepted (step-size factor as for
+    DP45).  Returns (m_new, t_new, dt_next)."""
+    if k1 is None:
+        k1 = prob.rhs(m, t)
+    while True:
+        y4, err = rkf45_attempt(prob, m, t, dt, k1, rtol, atol)
+        f = dp45_factor(err)
+        if err <= 1.0:
+            return (normalize(y4) if renorm else y4), t + dt, dt * f
+        dt = dt * f
+
+
+def relax(prob, m, tol=1e-3, max_steps=20000, dt0=1e-13, rtol=1e-5, atol=None, renorm=True, t0=0.0,
+          method="dp45"):
+    """Integrate with DP45 (or RKF45) until max |m x h| / Ms < tol (or
+    max_steps accepted steps).  Returns (m, steps, max_torque, t)."""
+    if method == "rkf45":
+        t, dt, steps = t0, dt0, 0
+        while True:
+            h = prob.heff(m, t)
+            tq = prob.max_torque(m, h)
+            if tq < tol or steps >= max_steps:
+                return m, steps, tq, t
+            k1 = llg_rhs(m, h, prob.alpha, prob.precession)
+            m, t, dt = rkf45_step(prob, m, t, dt, rtol, atol, renorm, k1)
+            steps += 1
     t = t0
     dt = dt0
     h = prob.heff(m, t)
-    k1 = llg_rhs(m, h, prob.alpha)
+    k1 = llg_rhs(m, h, prob.alpha, prob.precession)
     tq = prob.max_torque(m, h)
     steps = 0
     while tq >= tol and steps < max_steps:
