@@ -56,7 +56,13 @@ typedef enum {
                                error norm and time are accumulated in double     */
 } mm_precision;
 
-typedef enum { MM_RK4 = 0, MM_DP45 = 1 } mm_method;
+/* Explicit Runge-Kutta methods (Sec. 3): classic RK4 (fixed step), Dormand-
+ * Prince 5(4) with first-same-as-last, and Runge-Kutta-Fehlberg 4(5) -- the
+ * paper's default solver, which propagates the fourth-order solution and uses
+ * the fifth-order one only for the error.  The adaptive two share the error
+ * norm max |y_hi - y_lo| / (rtol + rtol max(|y_n|, |y_prop|)), accept if
+ * <= 1, and the step factor min(5, max(0.2, 0.9 err^-1/5)). */
+typedef enum { MM_RK4 = 0, MM_DP45 = 1, MM_RKF45 = 2 } mm_method;
 
 typedef struct {
     int nx, ny, nz;          /* cells per axis, each >= 1, nx*ny*nz < 2^31       */
@@ -150,15 +156,20 @@ mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], doub
  *   is <= 1, returns with the step accepted, *dt_inout set to the proposed next
  *   step (dt * min(5, max(0.2, 0.9 err^-1/5))).  Synchronises once per attempt
  *   to read the error norm.  MM_ESTEP if dt falls below 1e-22 s.
+ * MM_RKF45: Runge-Kutta-Fehlberg 4(5), same contract as MM_DP45; the
+ *   fourth-order solution is propagated and the error is measured against it
+ *   (no first-same-as-last stage: the first stage is evaluated at the new m).
  * On return *t_inout is advanced by the step taken.  m is renormalised to
  * unit length after each step.  MM_ENONFINITE if the step produced NaN/Inf
- * (DP45 only; RK4 checks nothing to stay asynchronous). */
+ * (adaptive methods only; RK4 checks nothing to stay asynchronous). */
 mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rtol,
                       double* t_inout);
 
-/* Relax (Sec. 3): DP45 steps with the material's damping until
- * max_i |m_i x h_i| / Ms_i < tol (the field of the last stage of the accepted
- * step), or max_steps accepted steps (then MM_ENOTCONVERGED).  Starts from
+/* Relax (Sec. 3): DP45 (or RKF45, see mm_set_llg_options) steps with the
+ * material's damping until max_i |m_i x h_i| / Ms_i < tol (DP45: the field of
+ * the last stage of the accepted step; RKF45: the field at the new m, which is
+ * the next step's first stage), or max_steps accepted steps (then
+ * MM_ENOTCONVERGED).  Starts from
  * dt = *dt_inout (1e-13 s if *dt_inout <= 0) and time *t_inout; both are
  * updated.  steps_out, torque_out: host outputs or NULL. */
 mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* dt_inout,
@@ -234,6 +245,14 @@ mm_status mm_batch_end(mm_batch* b, int* status, int* steps, double* torque);
 
 /* Copy a slot's magnetisation out (host copies synchronise). */
 mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
+
+/* Integrator options (Sec. 3): relax_method is the adaptive method mm_relax
+ * uses (MM_DP45, the default, or MM_RKF45); precession = 0 drops the m x h
+ * term of Eq. llg for every integrator of this state (the damping term keeps
+ * its factor gamma alpha / (1 + alpha^2)), as for ground-state searches;
+ * 1 (the default) restores it.  mm_llg_step_adjoint needs precession = 1
+ * (MM_EINVAL otherwise).  MM_EINVAL for other values. */
+mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession);
 
 /* Diagnostic (the paper has no counterpart): enqueue on the state's stream
  * one CTA that waits on an mbarrier nothing ever completes, polling it at most

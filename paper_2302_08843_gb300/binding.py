@@ -18,7 +18,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENONFINITE, MM_ESTEP, MM_ENOTCONVERGED
 STATUS_NAMES = ["MM_OK", "MM_EINVAL", "MM_ENOMEM", "MM_ECUDA", "MM_ENONFINITE", "MM_ESTEP",
                 "MM_ENOTCONVERGED", "MM_ETIMEOUT", "MM_ENOTSETUP"]
 MM_FP64, MM_FP32_FIELDS = 0, 1
-MM_RK4, MM_DP45 = 0, 1
+MM_RK4, MM_DP45, MM_RKF45 = 0, 1, 2
 
 # every exported symbol of include/mm.h
 EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m", "mm_get_m",
@@ -27,7 +27,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
-           "mm_selftest_wait_timeout")
+           "mm_selftest_wait_timeout", "mm_set_llg_options")
 
 
 class MMError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
         "mm_batch_begin": (i, [vp, i, d, d, i]),
         "mm_batch_query": (i, [vp, vp]),
         "mm_selftest_wait_timeout": (i, [vp, ctypes.c_uint]),
+        "mm_set_llg_options": (i, [vp, i, i]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -292,11 +293,16 @@ class State:
         """mm_selftest_wait_timeout: a device wait that runs out on this state's stream."""
         check(lib().mm_selftest_wait_timeout(self.h, int(spins)))
 
+    def set_llg_options(self, relax_method="dp45", precession=True):
+        """mm_set_llg_options: mm_relax's method ("dp45" or "rkf45") and the precession term."""
+        check(lib().mm_set_llg_options(self.h, MM_RKF45 if relax_method == "rkf45" else MM_DP45,
+                                       1 if precession else 0))
+
     def step(self, dt, t=0.0, method="rk4", rtol=1e-5):
-        """One mm_llg_step; returns (t_new, dt_next)."""
+        """One mm_llg_step (method "rk4", "dp45" or "rkf45"); returns (t_new, dt_next)."""
         dtc = ctypes.c_double(dt)
         tc = ctypes.c_double(t)
-        meth = MM_RK4 if method == "rk4" else MM_DP45
+        meth = {"rk4": MM_RK4, "dp45": MM_DP45, "rkf45": MM_RKF45}[method]
         check(lib().mm_llg_step(self.h, meth, ctypes.byref(dtc), float(rtol), ctypes.byref(tc)))
         return tc.value, dtc.value
 

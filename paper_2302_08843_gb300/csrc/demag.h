@@ -91,6 +91,8 @@ struct StageParams {
     double eb_k;
     double rtol, atol;
     int want_err, want_energy, want_torque;
+    int err_on_next;             // error scale max(|mn|, |next|) instead of max(|mn|, |m|)
+    int no_precession;           // drop the m x h summand of the LLG right-hand side
     double* partials;            // [number of blocks][kNPart]
     // the coefficients above in the field type (filled by launch_stage)
     T kcT[7], ckT, dtT, acc_bT;

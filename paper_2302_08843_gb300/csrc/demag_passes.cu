@@ -462,7 +462,9 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
                 const float al = p.alpha, gp = p.gp_u;
                 const float cx = my * hz - mz * hy, cy = mz * hx - mx * hz, cz = mx * hy - my * hx;
                 const float dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
-                const float kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
+                const float pc = p.no_precession ? 0.f : 1.f;
+                const float kx = gp * (pc * cx + al * dx_), ky = gp * (pc * cy + al * dy_),
+                            kz = gp * (pc * cz + al * dz_);
                 // RK combination: acc_out = acc_in + acc_b k;  next = mn + dt (kc0 kin0 + ck k)
                 accx[v] = p.acc_bT * kx + (p.acc_in ? ax_[v] : 0.f);
                 accy[v] = p.acc_bT * ky + (p.acc_in ? ay_[v] : 0.f);

@@ -175,7 +175,9 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
             const T gp = (!UNI && p.alpha_cell) ? (T)(-kGamma) / ((T)1 + al[v] * al[v]) : p.gp_u;
             const T cx = my[v] * hz - mz[v] * hy, cy = mz[v] * hx - mx[v] * hz, cz = mx[v] * hy - my[v] * hx;
             const T dx_ = my[v] * cz - mz[v] * cy, dy_ = mz[v] * cx - mx[v] * cz, dz_ = mx[v] * cy - my[v] * cx;
-            kx[v] = gp * (cx + al[v] * dx_); ky[v] = gp * (cy + al[v] * dy_); kz[v] = gp * (cz + al[v] * dz_);
+            const T pc = p.no_precession ? (T)0 : (T)1;
+            kx[v] = gp * (pc * cx + al[v] * dx_); ky[v] = gp * (pc * cy + al[v] * dy_);
+            kz[v] = gp * (pc * cz + al[v] * dz_);
             if (!(isfinite(kx[v]) && isfinite(ky[v]) && isfinite(kz[v]))) red_nf = 1.0;
             if (p.want_torque && Ms[v] != (T)0)
                 red_torque = fmax(red_torque, sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms[v]);
@@ -228,9 +230,14 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
             if (p.want_err) {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    const double scx = p.atol + p.rtol * fmax(fabs((double)m0x[v]), fabs((double)mx[v]));
-                    const double scy = p.atol + p.rtol * fmax(fabs((double)m0y[v]), fabs((double)my[v]));
-                    const double scz = p.atol + p.rtol * fmax(fabs((double)m0z[v]), fabs((double)mz[v]));
+                    // the solution the error is measured against: the stage input, or
+                    // the combination this stage writes (before renormalisation)
+                    const T ux = p.err_on_next ? m0x[v] + p.dtT * snx[v] : mx[v];
+                    const T uy = p.err_on_next ? m0y[v] + p.dtT * sny[v] : my[v];
+                    const T uz = p.err_on_next ? m0z[v] + p.dtT * snz[v] : mz[v];
+                    const double scx = p.atol + p.rtol * fmax(fabs((double)m0x[v]), fabs((double)ux));
+                    const double scy = p.atol + p.rtol * fmax(fabs((double)m0y[v]), fabs((double)uy));
+                    const double scz = p.atol + p.rtol * fmax(fabs((double)m0z[v]), fabs((double)uz));
                     const double r = fmax(fmax(fabs(p.dt * ex_[v]) / scx, fabs(p.dt * ey_[v]) / scy),
                                           fabs(p.dt * ez_[v]) / scz);
                     if (!isfinite(r)) red_nf = 1.0;

@@ -175,7 +175,10 @@ struct mm_state {
     mm_field_fn fn = nullptr;
     void* user = nullptr;
     bool have_m = false, have_mat = false, demag_ready = false, demag_off = false;
-    bool fsal = false;
+    bool fsal = false;             // K[0] holds the DP45 first stage of the next step
+    bool k1_exact = false;         // K[0] = f(m, t) at the current m (RKF45 needs exactly that)
+    int precession = 1;            // 0: LLG without the m x h term
+    mm_method relax_method = MM_DP45;
     bool s1_fresh = false;   // S1 holds the x-spectrum of Ms m for the current m (left by the fused RK4 path)
     bool use_fused = true;   // RK4 in FP32 may take the fused stage kernel
     KernelTimer timer;
@@ -273,6 +276,7 @@ template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, con
     zeeman_at(s, t, h);
     p.hx0 = (T)h[0]; p.hy0 = (T)h[1]; p.hz0 = (T)h[2];
     p.mn = (const T*)s->m;
+    p.no_precession = s->precession ? 0 : 1;
 }
 
 // demag field of m into s->hd
@@ -381,7 +385,7 @@ mm_status rk4_fused(mm_state* s, double dt, double t, bool* used) {
         MM_LAUNCHED();
     }
     s->s1_fresh = true;
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     *used = true;
     return MM_OK;
 }
@@ -418,7 +422,7 @@ template <typename T> mm_status rk4_impl(mm_state* s, double dt, double t) {
         }
         MM_TRY(run_stage<T>(s, p, false));
     }
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     return MM_OK;
 }
 
@@ -456,6 +460,7 @@ template <typename T> mm_status dp_first_stage(mm_state* s, double t, double* to
         if (s->h_scalars[R_NONFINITE] != 0.0) return fail(MM_ENONFINITE, "non-finite field or torque");
     }
     s->fsal = true;
+    s->k1_exact = true;
     return MM_OK;
 }
 
@@ -603,9 +608,95 @@ mm_status dp_step(mm_state* s, double* dt_inout, double rtol, double* t_inout, d
             MM_LAUNCHED();
             std::swap(s->K[0], s->K[6]);    // first same as last
             s->fsal = true;
+            s->k1_exact = false;            // f(y5) before renormalisation
             *t_inout += dt;
             *dt_inout = dt * f;
             if (torque_out) *torque_out = tq;
+            return MM_OK;
+        }
+        dt *= f;
+    }
+}
+
+// Runge-Kutta-Fehlberg 4(5) (E. Fehlberg, NASA TR R-315, 1969): six stages,
+// the fourth-order solution propagated, the fifth-order one for the error
+const double kRKF_C[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+const double kRKF_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+const double kRKF_B4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+const double kRKF_B5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+// one attempt from (m, t) with K[0] = f(m, t): K[1..5], the fourth-order y4
+// (returned in *y4buf, not renormalised) and the error norm against it
+template <typename T>
+mm_status rkf_attempt(mm_state* s, double t, double dt, double rtol, double* err, void** y4buf) {
+    const T* k0 = (const T*)s->K[0];
+    launch_combine<T>((const T*)s->m, &k0, &kRKF_A[1][0], 1, dt, (T*)s->mA, s->N, s->st);
+    MM_LAUNCHED();
+    void* ybuf[2] = {s->mA, s->mB};
+    int cur = 0;
+    for (int st = 1; st <= 5; ++st) {     // stage st computes K[st] from y_{st+1}
+        void* yin = ybuf[cur];
+        MM_TRY(run_demag<T>(s, yin));
+        StageParams<T> p;
+        fill_common<T>(s, p, yin, t + kRKF_C[st] * dt);
+        p.dt = dt;
+        p.k_out = (T*)s->K[st];
+        p.next = (T*)ybuf[1 - cur];
+        if (st < 5) {
+            for (int q = 0; q < st; ++q) { p.kin[q] = (const T*)s->K[q]; p.kc[q] = kRKF_A[st + 1][q]; }
+            p.nk = st;
+            p.ck = kRKF_A[st + 1][st];
+            MM_TRY(run_stage<T>(s, p, false));
+        } else {
+            // last stage: k6, y4 = m + dt sum b4 k, error sum (b5 - b4) k against y4
+            for (int q = 0; q < 5; ++q) {
+                p.kin[q] = (const T*)s->K[q];
+                p.kc[q] = kRKF_B4[q];
+                p.eb[q] = kRKF_B5[q] - kRKF_B4[q];
+            }
+            p.nk = 5;
+            p.ck = kRKF_B4[5];
+            p.eb_k = kRKF_B5[5] - kRKF_B4[5];
+            p.want_err = 1;
+            p.err_on_next = 1;
+            p.rtol = rtol;
+            p.atol = rtol;
+            MM_TRY(run_stage<T>(s, p, true));
+            *y4buf = ybuf[1 - cur];
+        }
+        cur = 1 - cur;
+    }
+    MM_TRY(read_scalars(s));
+    *err = s->h_scalars[R_ERR];
+    if (s->h_scalars[R_NONFINITE] != 0.0 || !std::isfinite(*err))
+        return fail(MM_ENONFINITE, "non-finite values in an RKF45 stage");
+    return MM_OK;
+}
+
+// attempts until one is accepted (same accept rule and step-size factor as DP45)
+template <typename T>
+mm_status rkf_step(mm_state* s, double* dt_inout, double rtol, double* t_inout) {
+    MM_TRY(ensure_dp_buffers(s));
+    if (!s->k1_exact) MM_TRY(dp_first_stage<T>(s, *t_inout, nullptr));
+    double dt = *dt_inout;
+    for (;;) {
+        if (!(dt >= 1e-22)) return fail(MM_ESTEP, "RKF45 step size underflow (dt = %g s)", dt);
+        double err = 0;
+        void* y4 = nullptr;
+        MM_TRY(rkf_attempt<T>(s, *t_inout, dt, rtol, &err, &y4));
+        const double f = dp_factor(err);
+        if (err <= 1.0) {
+            launch_renorm_copy<T>((const T*)y4, (T*)s->m, s->N, s->st);
+            MM_LAUNCHED();
+            s->fsal = s->k1_exact = false;
+            *t_inout += dt;
+            *dt_inout = dt * f;
             return MM_OK;
         }
         dt *= f;
@@ -933,7 +1024,7 @@ mm_status mm_set_material(mm_state* s, const mm_material* mat, int ptrs_on_devic
         MM_CUDA(cudaStreamSynchronize(s->st));
     }
     s->have_mat = true;
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     s->s1_fresh = false;
     return MM_OK;
 }
@@ -945,7 +1036,7 @@ mm_status mm_set_m(mm_state* s, const void* m, int on_device) {
     MM_CUDA(cudaMemcpyAsync(s->m, m, 3 * s->rsz * (size_t)s->N,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
     s->have_m = true;
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     s->s1_fresh = false;
     return MM_OK;
 }
@@ -968,7 +1059,7 @@ mm_status mm_set_zeeman(mm_state* s, const double h_const[3], mm_field_fn fn, vo
     s->fn = fn;
     s->user = user;
     MM_TRY(upload_real(s, weight, s->N, on_device, &s->zw));
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     return MM_OK;
 }
 
@@ -994,14 +1085,14 @@ mm_status mm_demag_setup(mm_state* s, int p_newell) {
     MM_CUDA(cudaStreamSynchronize(s->st));
     s->demag_ready = true;
     s->demag_off = false;
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     return MM_OK;
 }
 
 mm_status mm_demag_disable(mm_state* s) {
     MM_TRY(check_state(s));
     s->demag_off = true;
-    s->fsal = false;
+    s->fsal = s->k1_exact = false;
     return MM_OK;
 }
 
@@ -1029,6 +1120,11 @@ mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rt
         return s->prec == MM_FP64 ? dp_step<double>(s, dt_inout, rtol, t_inout, nullptr)
                                   : dp_step<float>(s, dt_inout, rtol, t_inout, nullptr);
     }
+    if (method == MM_RKF45) {
+        if (!(rtol > 0)) return fail(MM_EINVAL, "rtol must be > 0");
+        return s->prec == MM_FP64 ? rkf_step<double>(s, dt_inout, rtol, t_inout)
+                                  : rkf_step<float>(s, dt_inout, rtol, t_inout);
+    }
     return fail(MM_EINVAL, "unknown method %d", (int)method);
 }
 
@@ -1043,13 +1139,25 @@ mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* 
     double t = t_inout ? *t_inout : 0.0;
     double tq = 0.0;
     MM_TRY(ensure_dp_buffers(s));
-    MM_TRY(s->prec == MM_FP64 ? dp_first_stage<double>(s, t, &tq) : dp_first_stage<float>(s, t, &tq));
     int steps = 0;
     mm_status st = MM_OK;
-    while (tq >= tol && steps < max_steps) {
-        st = s->prec == MM_FP64 ? dp_step<double>(s, &dt, rtol, &t, &tq) : dp_step<float>(s, &dt, rtol, &t, &tq);
-        if (st != MM_OK) break;
-        ++steps;
+    if (s->relax_method == MM_RKF45) {
+        // the torque at each new m comes with the first stage of the next step
+        for (;;) {
+            st = s->prec == MM_FP64 ? dp_first_stage<double>(s, t, &tq) : dp_first_stage<float>(s, t, &tq);
+            if (st != MM_OK || tq < tol || steps >= max_steps) break;
+            st = s->prec == MM_FP64 ? rkf_step<double>(s, &dt, rtol, &t) : rkf_step<float>(s, &dt, rtol, &t);
+            if (st != MM_OK) break;
+            ++steps;
+        }
+    } else {
+        MM_TRY(s->prec == MM_FP64 ? dp_first_stage<double>(s, t, &tq) : dp_first_stage<float>(s, t, &tq));
+        while (tq >= tol && steps < max_steps) {
+            st = s->prec == MM_FP64 ? dp_step<double>(s, &dt, rtol, &t, &tq)
+                                    : dp_step<float>(s, &dt, rtol, &t, &tq);
+            if (st != MM_OK) break;
+            ++steps;
+        }
     }
     if (dt_inout) *dt_inout = dt;
     if (t_inout) *t_inout = t;
@@ -1066,10 +1174,22 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     if (!m_n || !lambda_np1 || !lambda_n) return fail(MM_EINVAL, "null m_n, lambda_np1 or lambda_n");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
     if (lambda_n == lambda_np1 || lambda_n == m_n) return fail(MM_EINVAL, "lambda_n must not alias the inputs");
+    if (!s->precession) return fail(MM_EINVAL, "the adjoint is written for the LLG right-hand side with precession");
     MM_TRY(ready_for_fields(s));
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)
                               : adjoint_impl<float>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t);
+}
+
+mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession) {
+    MM_TRY(check_state(s));
+    if (relax_method != MM_DP45 && relax_method != MM_RKF45)
+        return fail(MM_EINVAL, "relax method must be MM_DP45 or MM_RKF45");
+    if (precession != 0 && precession != 1) return fail(MM_EINVAL, "precession must be 0 or 1");
+    s->relax_method = relax_method;
+    if (s->precession != precession) s->fsal = s->k1_exact = false;
+    s->precession = precession;
+    return MM_OK;
 }
 
 mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins) {

@@ -1,0 +1,84 @@
+"""GPU parity of the Runge-Kutta-Fehlberg 4(5) integrator (the paper's
+default solver, Sec. 3) and of the LLG without the precession term: accepted
+step sizes and states against the oracle, relaxation without precession, the
+fused FP32 RK4 path with the term switched off, and the adjoint's refusal."""
+import numpy as np
+import pytest
+
+from gpu_util import FP32_TOL, oracle_problem, rel, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rkf45_steps_match_oracle():
+    from oracle.llg import rkf45_step
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.thin_film(n=(64, 32, 1))
+    s = setup_workload(w, "fp64")
+    prob = oracle_problem(w)
+    rtol = w.extra["rtol"]
+    m, t, dt = w.m0.copy(), 0.0, 1e-13
+    tg, dtg = 0.0, 1e-13
+    for step in range(12):
+        m, t, dt = rkf45_step(prob, m, t, dt, rtol)
+        tg, dtg = s.step(dtg, tg, "rkf45", rtol)
+        assert abs(tg - t) <= 1e-9 * t and abs(dtg - dt) <= 1e-6 * dt, (step, tg, t, dtg, dt)
+    assert rel(from_soa(to_host(s.get_m())), m) < 1e-9
+    s.close()
+
+
+def test_rkf45_relax_without_precession_matches_oracle():
+    from oracle.llg import Problem, relax
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import Workload, from_soa
+    rng = np.random.default_rng(31)
+    n = (16, 8, 2)
+    m0 = rng.normal(size=n + (3,))
+    m0 /= np.linalg.norm(m0, axis=-1, keepdims=True)
+    w = Workload("relax 16x8x2", n, (3e-9, 3e-9, 3e-9), Ms=8e5, A=1.3e-11, alpha=1.0, m0=m0)
+    s = setup_workload(w, "fp64")
+    s.set_llg_options(relax_method="rkf45", precession=False)
+    steps, tq, t, _ = s.relax(tol=1e-3, max_steps=5000, rtol=1e-5)
+    prob = Problem(n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, precession=False)
+    mr, steps_r, tq_r, t_r = relax(prob, m0, tol=1e-3, max_steps=5000, method="rkf45")
+    assert steps == steps_r
+    assert tq < 1e-3 and abs(tq - tq_r) < 1e-6 * tq_r
+    assert abs(t - t_r) <= 1e-9 * t_r
+    assert rel(from_soa(to_host(s.get_m())), mr) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 5 * FP32_TOL)])
+def test_rk4_without_precession(precision, tol):
+    """FP32 runs the fused stage kernel, FP64 the separate passes."""
+    from oracle.llg import Problem, rk4_step
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.plain_fp64()
+    s = setup_workload(w, precision)
+    s.set_llg_options(precession=False)
+    prob = Problem(w.n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, h_ext=w.h_ext, precession=False)
+    m, t = w.m0.copy(), 0.0
+    for _ in range(5):
+        m = rk4_step(prob, m, t, w.dt)
+        t, _ = s.step(w.dt, t, "rk4")
+    assert rel(from_soa(to_host(s.get_m())), m) < tol
+    s.close()
+
+
+def test_adjoint_needs_precession():
+    import torch
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import MMError, STATUS_NAMES, setup_workload
+    w = W.plain_fp64()
+    s = setup_workload(w, "fp64")
+    s.set_llg_options(precession=False)
+    m = s.get_m().clone()
+    lam = torch.zeros_like(m)
+    with pytest.raises(MMError) as e:
+        s.step_adjoint(m, lam, w.dt)
+    assert STATUS_NAMES[e.value.status] == "MM_EINVAL"
+    s.close()
