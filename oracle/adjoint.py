@@ -41,7 +41,10 @@ def _ms(prob):
 
 
 def rhs_vjp(prob, m, t, u):
-    """Returns ((df/dm)^T u, (df/dMs)^T u) at (m, t); the second is (nx, ny, nz)."""
+    """Returns ((df/dm)^T u, (df/dMs)^T u) at (m, t); the second is (nx, ny, nz).
+    Written for the LLG with precession and without DMI."""
+    if not getattr(prob, "precession", True) or np.any(np.asarray(getattr(prob, "D", 0.0)) != 0):
+        raise ValueError("rhs_vjp covers the LLG with precession and no DMI")
     alpha, gp = _gp(prob)
     Ms = _ms(prob)
     h = prob.heff(m, t)

@@ -9,6 +9,13 @@ anisotropy_field   : Sec. 4.1, first-order uniaxial anisotropy (the Ku1 term
 zeeman_field       : external field; Sec. 5.1 only shows ``ExternalField``.
                      It is given here as h(t) * w_i with an optional per-cell
                      weight w (1 where absent).
+dmi_field          : Sec. 4.3, the central-difference DMI field
+                     h_i = 2/(mu0 Ms_i) sum_{k=+-x,+-y,+-z} Dt_{i,k} e_k x m_{i+k} / (2 D_k)
+                     with the DMI vectors of the paper's table (e_{-k} = -e_k);
+                     a neighbour outside the grid is left out (the "ignore
+                     the non-existing values" option of Sec. 4.3).
+dmi_average        : Eq. D_avg, the effective coupling Dt of a link (see the
+                     readings there).
 linear_energy      : Eq. linear_energy_discrete, E = -1/2 mu0 V sum Ms m.h.
 zeeman_energy      : E = -mu0 V sum Ms m.h_ext (no 1/2; the paper gives no
                      Zeeman energy, this is the standard one for a field that
@@ -90,3 +97,50 @@ def zeeman_energy(m, h, Ms, V):
     """E = -mu0 V sum_i Ms_i m_i . h_i."""
     Ms = _grid(Ms, m.shape[:3])
     return -MU0 * V * float(np.sum(Ms * np.sum(m * h, axis=-1)))
+
+
+# DMI vectors (e_x, e_y, e_z) of the paper's table of DMI types
+DMI_VECTORS = {
+    "interface": ((0.0, 1.0, 0.0), (-1.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
+    "bulk": ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)),
+    "d2d": ((-1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 0.0)),
+}
+
+
+def dmi_average(Di, Dj):
+    """Eq. D_avg, element-wise.  Readings of the printed formula (garbled):
+    equal signs (Di Dj >= 0) take the harmonic mean 2 Di Dj / (Di + Dj)
+    (0 when both are 0), as the text says; opposite signs take the geometric
+    mean of the geometric mean sqrt(-Di Dj) and the arithmetic mean
+    |Di + Dj| / 2, with the sign of Di + Dj."""
+    Di = np.asarray(Di, dtype=np.float64)
+    Dj = np.asarray(Dj, dtype=np.float64)
+    prod = Di * Dj
+    s = Di + Dj
+    harm = np.zeros(np.broadcast(Di, Dj).shape)
+    np.divide(2.0 * prod, s, out=harm, where=(s != 0) & (prod >= 0))
+    opp = np.sign(s) * np.sqrt(np.sqrt(np.maximum(-prod, 0.0)) * np.abs(s) / 2.0)
+    return np.where(prod >= 0, harm, opp)
+
+
+def dmi_field(m, Ms, D, dx, kind="interface"):
+    """h_i = 2/(mu0 Ms_i) sum_k Dt_{i,k} e_k x m_{i+k} / (2 D_k), k = +-x, +-y, +-z."""
+    shape = m.shape[:3]
+    D = _grid(D, shape)
+    vecs = DMI_VECTORS[kind]
+    h = np.zeros_like(m)
+    for ax in range(3):
+        e = np.asarray(vecs[ax], dtype=np.float64)
+        n = shape[ax]
+        if n < 2 or not e.any():
+            continue
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, n - 1)
+        hi[ax] = slice(1, n)
+        lo, hi = tuple(lo), tuple(hi)
+        Dt = dmi_average(D[lo], D[hi]) / (2.0 * float(dx[ax]))
+        eb = np.broadcast_to(e, m[hi].shape)
+        h[lo] += Dt[..., None] * np.cross(eb, m[hi])      # cell i, neighbour +k, vector +e
+        h[hi] -= Dt[..., None] * np.cross(eb, m[lo])      # cell i+k, neighbour -k, vector -e
+    return h * (2.0 / MU0) * _inv_ms(Ms, shape)[..., None]

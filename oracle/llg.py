@@ -37,7 +37,7 @@ import numpy as np
 
 from .constants import GAMMA
 from .demag import demag_fft, magnetization, tensor_spectrum
-from .fields import (anisotropy_field, exchange_field, linear_energy,
+from .fields import (anisotropy_field, dmi_field, exchange_field, linear_energy,
                      zeeman_energy, zeeman_field)
 from .newell import demag_tensor
 
@@ -59,7 +59,8 @@ class Problem:
     (nx, ny, nz) multiplier of the external field; p: Newell radius."""
 
     def __init__(self, n, dx, Ms, A, alpha, Ku1=0.0, ku_axis=(1.0, 0.0, 0.0),
-                 h_ext=(0.0, 0.0, 0.0), h_ext_weight=None, p=20, demag=True, Nt=None, precession=True):
+                 h_ext=(0.0, 0.0, 0.0), h_ext_weight=None, p=20, demag=True, Nt=None, precession=True,
+                 D=0.0, dmi="interface"):
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
         self.V = self.dx[0] * self.dx[1] * self.dx[2]
@@ -72,6 +73,8 @@ class Problem:
         self.h_ext_weight = h_ext_weight
         self.demag = demag
         self.precession = precession
+        self.D = D
+        self.dmi = dmi
         if demag:
             self.Nt = demag_tensor(self.n, self.dx, p) if Nt is None else Nt
             self.Nhat = tensor_spectrum(self.Nt, self.n)
@@ -88,6 +91,7 @@ class Problem:
         terms["exchange"] = exchange_field(m, self.Ms, self.A, self.dx)
         terms["anisotropy"] = anisotropy_field(m, self.Ms, self.Ku1, self.ku_axis)
         terms["zeeman"] = zeeman_field(self.h_ext_at(t), self.n, self.h_ext_weight)
+        terms["dmi"] = dmi_field(m, self.Ms, self.D, self.dx, self.dmi)
         # reading: a cell with Ms = 0 carries no field at all (the nan_to_num
         # of Sec. 4.1 extended to every term)
         ms = np.broadcast_to(np.asarray(self.Ms, dtype=np.float64), self.n)
@@ -98,15 +102,16 @@ class Problem:
 
     def heff(self, m, t):
         terms = self.field_terms(m, t)
-        return terms["demag"] + terms["exchange"] + terms["anisotropy"] + terms["zeeman"]
+        return terms["demag"] + terms["exchange"] + terms["anisotropy"] + terms["zeeman"] + terms["dmi"]
 
     def energies(self, m, t):
-        """(E_demag, E_exchange, E_anisotropy, E_zeeman) in J."""
+        """(E_demag, E_exchange, E_anisotropy, E_zeeman, E_dmi) in J."""
         terms = self.field_terms(m, t)
         return (linear_energy(m, terms["demag"], self.Ms, self.V),
                 linear_energy(m, terms["exchange"], self.Ms, self.V),
                 linear_energy(m, terms["anisotropy"], self.Ms, self.V),
-                zeeman_energy(m, terms["zeeman"], self.Ms, self.V))
+                zeeman_energy(m, terms["zeeman"], self.Ms, self.V),
+                linear_energy(m, terms["dmi"], self.Ms, self.V))
 
     def rhs(self, m, t):
         return llg_rhs(m, self.heff(m, t), self.alpha, self.precession)

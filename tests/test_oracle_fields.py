@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle.constants import MU0
-from oracle.fields import (anisotropy_field, exchange_field, linear_energy,
+from oracle.fields import (anisotropy_field, dmi_average, dmi_field, exchange_field, linear_energy,
                            zeeman_energy, zeeman_field)
 
 
@@ -124,3 +124,70 @@ def test_zeeman_field_and_energy():
     w = np.array([[[1.0], [0.0]], [[0.5], [2.0]]])
     hw = zeeman_field((1.0, 2.0, 3.0), n, w)
     assert np.allclose(hw[1, 0, 0], [0.5, 1.0, 1.5]) and np.all(hw[0, 1, 0] == 0)
+
+
+# ---------------------------------------------------------------- DMI ----
+
+def test_dmi_average():
+    assert dmi_average(3e-3, 3e-3) == pytest.approx(3e-3, rel=1e-15)
+    assert dmi_average(2e-3, 1e-3) == pytest.approx(2 * 2e-3 * 1e-3 / 3e-3, rel=1e-15)
+    assert dmi_average(-2e-3, -1e-3) == pytest.approx(-2 * 2e-3 * 1e-3 / 3e-3, rel=1e-15)
+    assert dmi_average(2e-3, 0.0) == 0.0 and dmi_average(0.0, 0.0) == 0.0
+    assert dmi_average(2e-3, -2e-3) == 0.0
+    # opposite signs: sign of the sum times sqrt(sqrt(-Di Dj) |Di + Dj| / 2)
+    v = dmi_average(4e-3, -1e-3)
+    assert v == pytest.approx(np.sqrt(np.sqrt(4e-6) * 3e-3 / 2), rel=1e-14)
+    assert dmi_average(-1e-3, 4e-3) == v and dmi_average(-4e-3, 1e-3) == -v
+
+
+@pytest.mark.parametrize("kind", ["interface", "bulk", "d2d"])
+def test_dmi_uniform_m_has_no_interior_field(kind):
+    n = (6, 5, 4)
+    m = np.broadcast_to(np.array([0.36, 0.48, 0.8]), n + (3,)).copy()
+    h = dmi_field(m, 8e5, 3e-3, (2e-9, 2e-9, 2e-9), kind)
+    assert np.max(np.abs(h[1:-1, 1:-1, 1:-1])) < 1e-9
+    assert np.max(np.abs(h)) > 1e3      # the boundary cells miss a neighbour
+
+
+@pytest.mark.parametrize("kind,axis,plane,sign", [
+    ("interface", 0, (0, 2), 1.0),      # m = (cos qx, 0, sin qx)
+    ("interface", 1, (1, 2), 1.0),      # m = (0, cos qy, sin qy)
+    ("d2d", 0, (1, 2), 1.0),            # m = (0, cos qx, sin qx)
+    ("d2d", 1, (0, 2), 1.0),            # m = (cos qy, 0, sin qy)
+    ("bulk", 0, (1, 2), -1.0),          # m = (0, cos qx, sin qx)
+    ("bulk", 2, (0, 1), -1.0),          # m = (cos qz, sin qz, 0)
+])
+def test_dmi_spirals_closed_form(kind, axis, plane, sign):
+    """For a spiral along one axis the central difference is exact:
+    (m_{i+1} - m_{i-1}) / (2 D) = sin(q D)/D dm/d(qx), and the DMI vector
+    turns it back onto m, so h = +-(2 D / (mu0 Ms)) sin(q D)/D m inside."""
+    N, d, q, Ms, Dm = 24, 2e-9, 2 * np.pi / 17e-9, 8e5, 3e-3
+    n = [1, 1, 1]
+    n[axis] = N
+    x = (np.arange(N) * d).reshape(n)
+    m = np.zeros(tuple(n) + (3,))
+    m[..., plane[0]] = np.cos(q * x)
+    m[..., plane[1]] = np.sin(q * x)
+    h = dmi_field(m, Ms, Dm, (d, d, d), kind)
+    expect = sign * 2 * Dm / (MU0 * Ms) * np.sin(q * d) / d * m
+    inner = [slice(None)] * 3
+    inner[axis] = slice(1, N - 1)
+    inner = tuple(inner)
+    assert np.max(np.abs(h[inner] - expect[inner])) < 1e-9 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("kind", ["interface", "bulk", "d2d"])
+def test_dmi_operator_is_self_adjoint(kind):
+    """sum Ms u . h(v) = sum Ms v . h(u) for per-cell D and Ms: the DMI energy
+    is a linear-field energy (Eq. linear_energy_discrete)."""
+    rng = np.random.default_rng(5)
+    n = (5, 4, 3)
+    Ms = rng.uniform(4e5, 9e5, size=n)
+    D = rng.uniform(-3e-3, 3e-3, size=n)
+    u = rng.normal(size=n + (3,))
+    v = rng.normal(size=n + (3,))
+    dx = (2e-9, 3e-9, 2.5e-9)
+    a = np.sum(Ms[..., None] * u * dmi_field(v, Ms, D, dx, kind))
+    b = np.sum(Ms[..., None] * v * dmi_field(u, Ms, D, dx, kind))
+    assert abs(a - b) < 1e-12 * (abs(a) + abs(b))
+
