@@ -64,6 +64,11 @@ typedef enum {
  * <= 1, and the step factor min(5, max(0.2, 0.9 err^-1/5)). */
 typedef enum { MM_RK4 = 0, MM_DP45 = 1, MM_RKF45 = 2 } mm_method;
 
+/* DMI types of the paper's table (Sec. 4.3), by their DMI vectors
+ * (e_x, e_y, e_z): interface (e_y, -e_x, 0), bulk (e_x, e_y, e_z),
+ * D2d (-e_x, e_y, 0). */
+typedef enum { MM_DMI_NONE = 0, MM_DMI_INTERFACE = 1, MM_DMI_BULK = 2, MM_DMI_D2D = 3 } mm_dmi_kind;
+
 typedef struct {
     int nx, ny, nz;          /* cells per axis, each >= 1, nx*ny*nz < 2^31       */
     double dx, dy, dz;       /* cell size in metres, > 0                         */
@@ -137,15 +142,15 @@ mm_status mm_demag_disable(mm_state* s);
 
 /* One effective-field evaluation (Sec. 4) at time t on m (device pointer in
  * the state's layout and type, or NULL for the state's m).  h_out: device
- * buffer for the total field or NULL.  E_out: host array of 4 doubles or NULL,
- * receives (E_demag, E_exchange, E_anisotropy, E_zeeman) in joules
- * (Eq. linear_energy_discrete for the first three, -mu0 V sum Ms m.h for
+ * buffer for the total field or NULL.  E_out: host array of 5 doubles or NULL,
+ * receives (E_demag, E_exchange, E_anisotropy, E_zeeman, E_dmi) in joules
+ * (Eq. linear_energy_discrete for the linear terms, -mu0 V sum Ms m.h for
  * Zeeman); asking for E_out synchronises the stream.  torque_out: host double
  * or NULL, receives max over cells of |m x h| / Ms (synchronises).  When
  * E_out or torque_out is asked for and a cell's field or torque is not
  * finite, the call returns MM_ENONFINITE (h_out and the scalars are still
  * written). */
-mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], double t,
+mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[5], double t,
                   double* torque_out);
 
 /* Advance the state by one step of the LLG equation (Eq. llg).
@@ -245,6 +250,18 @@ mm_status mm_batch_end(mm_batch* b, int* status, int* steps, double* torque);
 
 /* Copy a slot's magnetisation out (host copies synchronise). */
 mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
+
+/* DMI field (Sec. 4.3): h_i = 2/(mu0 Ms_i) sum_{k=+-x,+-y,+-z} Dt_{i,k}
+ * e_k x m_{i+k} / (2 d_k), e_{-k} = -e_k, with the DMI vectors of `kind`; a
+ * neighbour outside the grid is left out.  D in J/m^2 for every cell, or
+ * D_cell (nx*ny*nz doubles, [nz][ny][nx], host or device per on_device,
+ * copied) per cell, each link then taking the average Dt of Eq. D_avg (the
+ * harmonic mean for equal signs; for opposite signs the geometric mean of the
+ * geometric and the arithmetic mean, with the sign of the sum).  Its energy
+ * is the fifth entry of mm_heff's E_out.  MM_DMI_NONE switches the term off.
+ * The adjoint does not cover DMI (mm_llg_step_adjoint returns MM_EINVAL).
+ * MM_EINVAL for an unknown kind or a non-finite D. */
+mm_status mm_set_dmi(mm_state* s, mm_dmi_kind kind, double D, const double* D_cell, int on_device);
 
 /* Integrator options (Sec. 3): relax_method is the adaptive method mm_relax
  * uses (MM_DP45, the default, or MM_RKF45); precession = 0 drops the m x h

@@ -27,7 +27,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
-           "mm_selftest_wait_timeout", "mm_set_llg_options")
+           "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi")
 
 
 class MMError(RuntimeError):
@@ -96,6 +96,7 @@ def lib():
         "mm_batch_query": (i, [vp, vp]),
         "mm_selftest_wait_timeout": (i, [vp, ctypes.c_uint]),
         "mm_set_llg_options": (i, [vp, i, i]),
+        "mm_set_dmi": (i, [vp, i, d, vp, i]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -278,7 +279,7 @@ class State:
             m = self._as_field(m)
         if h_out is None:
             h_out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
-        E = (ctypes.c_double * 4)() if energies else None
+        E = (ctypes.c_double * 5)() if energies else None
         tq = ctypes.c_double() if torque else None
         check(lib().mm_heff(self.h, None if m is None else m.data_ptr(), h_out.data_ptr(), E, float(t),
                             ctypes.byref(tq) if torque else None))
@@ -292,6 +293,16 @@ class State:
     def selftest_wait_timeout(self, spins=1 << 16):
         """mm_selftest_wait_timeout: a device wait that runs out on this state's stream."""
         check(lib().mm_selftest_wait_timeout(self.h, int(spins)))
+
+    DMI_KINDS = {None: 0, "none": 0, "interface": 1, "bulk": 2, "d2d": 3}
+
+    def set_dmi(self, kind="interface", D=0.0, D_cell=None):
+        """mm_set_dmi: kind "interface", "bulk", "d2d" or None; D_cell float64
+        numpy (nz, ny, nx) or a float64 CUDA tensor."""
+        if isinstance(D_cell, np.ndarray):
+            D_cell = np.ascontiguousarray(D_cell, dtype=np.float64)     # kept alive through the call
+        p, dev = _ptr(D_cell)
+        check(lib().mm_set_dmi(self.h, self.DMI_KINDS[kind], float(D), p, dev))
 
     def set_llg_options(self, relax_method="dp45", precession=True):
         """mm_set_llg_options: mm_relax's method ("dp45" or "rkf45") and the precession term."""

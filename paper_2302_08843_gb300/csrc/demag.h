@@ -58,7 +58,7 @@ void launch_adj_renorm(const T* y, const T* lam, T* lam_y, T* lam_acc, T* u, dou
 // number of doubles per block in the reduction partials
 constexpr int kNPart = 8;
 // partial / scalar slots
-enum { R_TORQUE = 0, R_EDEM = 1, R_EEX = 2, R_EANI = 3, R_EZEE = 4, R_ERR = 5, R_NONFINITE = 6 };
+enum { R_TORQUE = 0, R_EDEM = 1, R_EEX = 2, R_EANI = 3, R_EZEE = 4, R_ERR = 5, R_NONFINITE = 6, R_EDMI = 7 };
 
 template <typename T>
 struct StageParams {
@@ -92,6 +92,10 @@ struct StageParams {
     double rtol, atol;
     int want_err, want_energy, want_torque;
     int err_on_next;             // error scale max(|mn|, |next|) instead of max(|mn|, |m|)
+    int dmi;                     // DMI term on (Sec. 4.3)
+    const T* D_cell; T D;        // DMI strength per cell (links averaged) or uniform
+    T dmi_e[9];                  // DMI vectors e_x, e_y, e_z (each 3 components)
+    T i2dx, i2dy, i2dz;          // 1 / (2 d) per axis
     int no_precession;           // drop the m x h summand of the LLG right-hand side
     double* partials;            // [number of blocks][kNPart]
     // the coefficients above in the field type (filled by launch_stage)

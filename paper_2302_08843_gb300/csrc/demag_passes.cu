@@ -296,7 +296,7 @@ p5_x_tma(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float* __restr
 // next stage's x-spectrum, written over this tile's rows of S1.
 // NSLOT TMA slots: with one, the next tile's load is issued as soon as this
 // tile is staged and has both transforms and the cell updates to land.
-template <int LX, int TY, int NSLOT, int PAD, int MINB>
+template <int LX, int TY, int NSLOT, int PAD, int MINB, bool DMI>
 __global__ void __launch_bounds__((3 * TY / 2) * Fft<float, LX, +1, false>::TPL, MINB)
 k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __restrict__ S1, StageParams<float> p,
          int kxb, int nboxes, int slot_bytes) {
@@ -404,31 +404,56 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             const float2 cx2 = m2[i2], cy2 = m2[N2 + i2], cz2 = m2[2 * N2 + i2];
             const float mxv[2] = {cx2.x, cx2.y}, myv[2] = {cy2.x, cy2.y}, mzv[2] = {cz2.x, cz2.y};
             float sx[2] = {0.f, 0.f}, sy[2] = {0.f, 0.f}, sz[2] = {0.f, 0.f};
+            // DMI sums (uniform D, Sec. 4.3): per cell, sum over axes of e_a x (m_{+a} - m_{-a}) D / (2 d_a)
+            float qx[2] = {0.f, 0.f}, qy[2] = {0.f, 0.f}, qz[2] = {0.f, 0.f};
             {   // x links
                 const float wx = p.A * p.idx2;
                 // inner link between the two cells
                 sx[0] += wx * (mxv[1] - mxv[0]); sy[0] += wx * (myv[1] - myv[0]); sz[0] += wx * (mzv[1] - mzv[0]);
                 sx[1] += wx * (mxv[0] - mxv[1]); sy[1] += wx * (myv[0] - myv[1]); sz[1] += wx * (mzv[0] - mzv[1]);
+                float dl[3] = {0.f, 0.f, 0.f}, dr[3] = {0.f, 0.f, 0.f};   // DMI: m_{+x} - m_{-x} per cell
+                if constexpr (DMI) {
+                    dl[0] = mxv[1]; dl[1] = myv[1]; dl[2] = mzv[1];
+                    dr[0] = -mxv[0]; dr[1] = -myv[0]; dr[2] = -mzv[0];
+                }
                 if (x0 > 0) {
-                    sx[0] += wx * (m[i - 1] - mxv[0]); sy[0] += wx * (m[N + i - 1] - myv[0]);
-                    sz[0] += wx * (m[2 * N + i - 1] - mzv[0]);
+                    const float ax = m[i - 1], ay = m[N + i - 1], az = m[2 * N + i - 1];
+                    sx[0] += wx * (ax - mxv[0]); sy[0] += wx * (ay - myv[0]); sz[0] += wx * (az - mzv[0]);
+                    if constexpr (DMI) { dl[0] -= ax; dl[1] -= ay; dl[2] -= az; }
                 }
                 if (x0 + 2 < nx) {
-                    sx[1] += wx * (m[i + 2] - mxv[1]); sy[1] += wx * (m[N + i + 2] - myv[1]);
-                    sz[1] += wx * (m[2 * N + i + 2] - mzv[1]);
+                    const float ax = m[i + 2], ay = m[N + i + 2], az = m[2 * N + i + 2];
+                    sx[1] += wx * (ax - mxv[1]); sy[1] += wx * (ay - myv[1]); sz[1] += wx * (az - mzv[1]);
+                    if constexpr (DMI) { dr[0] += ax; dr[1] += ay; dr[2] += az; }
+                }
+                if constexpr (DMI) {
+                    const float c = p.D * p.i2dx;
+                    const float* e = &p.dmi_e[0];
+                    qx[0] += c * (e[1] * dl[2] - e[2] * dl[1]); qy[0] += c * (e[2] * dl[0] - e[0] * dl[2]);
+                    qz[0] += c * (e[0] * dl[1] - e[1] * dl[0]);
+                    qx[1] += c * (e[1] * dr[2] - e[2] * dr[1]); qy[1] += c * (e[2] * dr[0] - e[0] * dr[2]);
+                    qz[1] += c * (e[0] * dr[1] - e[1] * dr[0]);
                 }
             }
-#define MM_F2LINK(COND, OFF2, ID2)                                                             \
+#define MM_F2LINK(COND, OFF2, ID2, SIGN, EOFF, I2D)                                            \
             if (COND) {                                                                        \
                 const float w = p.A * (ID2);                                                   \
                 const float2 a = m2[i2 + (OFF2)], b = m2[N2 + i2 + (OFF2)], c = m2[2 * N2 + i2 + (OFF2)]; \
                 sx[0] += w * (a.x - mxv[0]); sy[0] += w * (b.x - myv[0]); sz[0] += w * (c.x - mzv[0]); \
                 sx[1] += w * (a.y - mxv[1]); sy[1] += w * (b.y - myv[1]); sz[1] += w * (c.y - mzv[1]); \
+                if constexpr (DMI) {                                                           \
+                    const float g = (SIGN) * p.D * (I2D);                                      \
+                    const float* e = &p.dmi_e[EOFF];                                           \
+                    qx[0] += g * (e[1] * c.x - e[2] * b.x); qy[0] += g * (e[2] * a.x - e[0] * c.x); \
+                    qz[0] += g * (e[0] * b.x - e[1] * a.x);                                    \
+                    qx[1] += g * (e[1] * c.y - e[2] * b.y); qy[1] += g * (e[2] * a.y - e[0] * c.y); \
+                    qz[1] += g * (e[0] * b.y - e[1] * a.y);                                    \
+                }                                                                              \
             }
-            MM_F2LINK(y > 0, -(nx >> 1), p.idy2)
-            MM_F2LINK(y < ny - 1, (nx >> 1), p.idy2)
-            MM_F2LINK(z > 0, -((nx * ny) >> 1), p.idz2)
-            MM_F2LINK(z < nz - 1, ((nx * ny) >> 1), p.idz2)
+            MM_F2LINK(y > 0, -(nx >> 1), p.idy2, -1.f, 3, p.i2dy)
+            MM_F2LINK(y < ny - 1, (nx >> 1), p.idy2, 1.f, 3, p.i2dy)
+            MM_F2LINK(z > 0, -((nx * ny) >> 1), p.idz2, -1.f, 6, p.i2dz)
+            MM_F2LINK(z < nz - 1, ((nx * ny) >> 1), p.idz2, 1.f, 6, p.i2dz)
 #undef MM_F2LINK
             const float2 n0 = reinterpret_cast<const float2*>(p.mn)[i2];
             const float2 n1 = reinterpret_cast<const float2*>(p.mn)[N2 + i2];
@@ -447,6 +472,7 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             for (int v = 0; v < 2; ++v) {
                 const float mx = mxv[v], my = myv[v], mz = mzv[v];
                 float hx = p.cex_u * sx[v], hy = p.cex_u * sy[v], hz = p.cex_u * sz[v];
+                if constexpr (DMI) { hx += p.cex_u * qx[v]; hy += p.cex_u * qy[v]; hz += p.cex_u * qz[v]; }
                 if (p.Ku != 0.f) {
                     float ex = p.ex, ey = p.ey, ez = p.ez;
                     if (p.grain) {
@@ -1335,7 +1361,7 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         return false;
     } else {
         if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
-        if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.Ms == 0.f || p.hd || p.k_out ||
+        if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f || p.hd || p.k_out ||
             p.h_out || p.want_err || p.want_energy || p.want_torque || !p.next || p.nk > 1)
             return false;
         if (d.nx % 2 != 0) return false;
@@ -1351,7 +1377,8 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         const int slot_bytes = (int)(((size_t)nb * w * TY * 3 * sizeof(float2) + 127) / 128 * 128);
         const size_t sm = kK5Slots * (size_t)slot_bytes + (size_t)L * (NL + kK5Pad) * sizeof(float2) + 16;
         if (sm > 220 * 1024) return false;
-        auto k = k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks>;
+        auto k = p.dmi ? k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks, true>
+                       : k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks, false>;
         set_smem(k, sm);
         const int threads = NL * Fft<float, L, +1, false>::TPL;
         if (threads > 1024) return false;
@@ -1442,7 +1469,7 @@ bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cu
 
 bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
     if (!d.err || d.LX < 16 || d.LX > 4096 || d.nx % 2 != 0) return false;
-    if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.Ms == 0.f) return false;
+    if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f) return false;
     const int threads = (3 * kK5Rows / 2) * (d.LX / 16);
     return threads <= 1024;
 }

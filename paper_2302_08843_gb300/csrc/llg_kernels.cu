@@ -80,7 +80,22 @@ constexpr int kBX = 64, kBY = 4;   // threads per block: 64 along x, 4 rows of y
 // Requires nx % VEC == 0 (all of a thread's cells in one row).
 // UNI: Ms, A, Ku and alpha are uniform scalars (easy axes may still vary by
 // grain); the per-cell branches for material maps then compile away.
-template <typename T, int VEC, bool UNI>
+// Eq. D_avg as read: harmonic mean for equal signs, otherwise the geometric mean
+// of the geometric and the arithmetic mean with the sign of the sum
+template <typename T> __device__ __forceinline__ T dmi_avg(T a, T b) {
+    const T prod = a * b, s = a + b;
+    if (prod >= (T)0) return s != (T)0 ? (T)2 * prod / s : (T)0;
+    return copysign(sqrt(sqrt(-prod) * fabs(s) * (T)0.5), s);
+}
+
+// out += e x w
+template <typename T> __device__ __forceinline__ void cross_add(const T* e, T wx, T wy, T wz, T& ox, T& oy, T& oz) {
+    ox += e[1] * wz - e[2] * wy;
+    oy += e[2] * wx - e[0] * wz;
+    oz += e[0] * wy - e[1] * wx;
+}
+
+template <typename T, int VEC, bool UNI, bool DMI>
 __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> p) {
     using LV = Vec<T, VEC>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -88,7 +103,8 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
     const int x0 = (blockIdx.x * kBX + threadIdx.x) * VEC;
     const int y = blockIdx.y * kBY + threadIdx.y;
     const int z = blockIdx.z;
-    double red_torque = 0.0, red_e0 = 0.0, red_e1 = 0.0, red_e2 = 0.0, red_e3 = 0.0, red_err = 0.0, red_nf = 0.0;
+    double red_torque = 0.0, red_e0 = 0.0, red_e1 = 0.0, red_e2 = 0.0, red_e3 = 0.0, red_e4 = 0.0, red_err = 0.0,
+           red_nf = 0.0;
     if (x0 < nx && y < ny) {
         const int i = x0 + nx * (y + ny * z);
         const int sy = nx, sz = nx * ny;
@@ -138,6 +154,51 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
         MM_VLINK(z > 0, -sz, p.idz2)
         MM_VLINK(z < nz - 1, sz, p.idz2)
 #undef MM_VLINK
+        // DMI (Sec. 4.3): dm_i = sum_axes e_a x (Dt_+ m_{i+a} - Dt_- m_{i-a}) / (2 d_a); a neighbour
+        // outside the grid is left out; Dt the link average of D (D itself when uniform)
+        T dmx[VEC], dmy[VEC], dmz[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) { dmx[v] = 0; dmy[v] = 0; dmz[v] = 0; }
+        if constexpr (DMI) {
+            const bool d_cell = p.D_cell != nullptr;
+            T Dc[VEC];
+            if (d_cell) LV::ld(p.D_cell + i, Dc); else { for (int v = 0; v < VEC; ++v) Dc[v] = p.D; }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int x = x0 + v;
+                T wx = 0, wy = 0, wz = 0;
+                if (x < nx - 1) {
+                    T nbx, nby, nbz, Dn;
+                    if (v < VEC - 1) { nbx = mx[v + 1]; nby = my[v + 1]; nbz = mz[v + 1]; Dn = Dc[v + 1]; }
+                    else { nbx = m[i + VEC]; nby = m[N + i + VEC]; nbz = m[2 * N + i + VEC]; Dn = d_cell ? p.D_cell[i + VEC] : p.D; }
+                    const T Dt = d_cell ? dmi_avg(Dc[v], Dn) : p.D;
+                    wx += Dt * nbx; wy += Dt * nby; wz += Dt * nbz;
+                }
+                if (x > 0) {
+                    T nbx, nby, nbz, Dn;
+                    if (v > 0) { nbx = mx[v - 1]; nby = my[v - 1]; nbz = mz[v - 1]; Dn = Dc[v - 1]; }
+                    else { nbx = m[i - 1]; nby = m[N + i - 1]; nbz = m[2 * N + i - 1]; Dn = d_cell ? p.D_cell[i - 1] : p.D; }
+                    const T Dt = d_cell ? dmi_avg(Dc[v], Dn) : p.D;
+                    wx -= Dt * nbx; wy -= Dt * nby; wz -= Dt * nbz;
+                }
+                cross_add(&p.dmi_e[0], wx * p.i2dx, wy * p.i2dx, wz * p.i2dx, dmx[v], dmy[v], dmz[v]);
+            }
+#define MM_DLINK(COND, OFF, SIGN, E, I2D)                                                  \
+            if (COND) {                                                                    \
+                T nbx[VEC], nby[VEC], nbz[VEC], Dn[VEC];                                   \
+                LV::ld(m + i + (OFF), nbx); LV::ld(m + N + i + (OFF), nby); LV::ld(m + 2 * N + i + (OFF), nbz); \
+                if (d_cell) LV::ld(p.D_cell + i + (OFF), Dn);                              \
+                _Pragma("unroll") for (int v = 0; v < VEC; ++v) {                           \
+                    const T Dt = (SIGN) * (d_cell ? dmi_avg(Dc[v], Dn[v]) : p.D) * (I2D);  \
+                    cross_add(E, Dt * nbx[v], Dt * nby[v], Dt * nbz[v], dmx[v], dmy[v], dmz[v]); \
+                }                                                                          \
+            }
+            MM_DLINK(y > 0, -sy, (T)-1, &p.dmi_e[3], p.i2dy)
+            MM_DLINK(y < ny - 1, sy, (T)1, &p.dmi_e[3], p.i2dy)
+            MM_DLINK(z > 0, -sz, (T)-1, &p.dmi_e[6], p.i2dz)
+            MM_DLINK(z < nz - 1, sz, (T)1, &p.dmi_e[6], p.i2dz)
+#undef MM_DLINK
+        }
         T Ku[VEC], al[VEC], zw[VEC], hdx[VEC], hdy[VEC], hdz[VEC];
         if (!UNI && p.Ku_cell) LV::ld(p.Ku_cell + i, Ku); else { for (int v = 0; v < VEC; ++v) Ku[v] = p.Ku; }
         if (!UNI && p.alpha_cell) LV::ld(p.alpha_cell + i, al); else { for (int v = 0; v < VEC; ++v) al[v] = p.alpha; }
@@ -149,12 +210,13 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             T hx = 0, hy = 0, hz = 0, hex = 0, hey = 0, hez = 0, hax = 0, hay = 0, haz = 0, hzx = 0, hzy = 0, hzz = 0;
-            T hdxv = 0, hdyv = 0, hdzv = 0;
+            T hdxv = 0, hdyv = 0, hdzv = 0, hmx = 0, hmy = 0, hmz = 0;
             if (UNI || Ms[v] != (T)0) {
                 const bool uni = UNI || !p.Ms_cell;
                 const T inv = uni ? (T)0 : (T)1 / Ms[v];
                 const T cex = uni ? p.cex_u : (T)(2.0 / kMu0) * inv;
                 hex = cex * sx[v]; hey = cex * sy_[v]; hez = cex * sz_[v];
+                if constexpr (DMI) { hmx = cex * dmx[v]; hmy = cex * dmy[v]; hmz = cex * dmz[v]; }
                 if (UNI ? (p.Ku != (T)0) : (Ku[v] != (T)0)) {
                     T ex = p.ex, ey = p.ey, ez = p.ez;
                     if (p.grain) {
@@ -167,9 +229,9 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
                 }
                 hzx = zw[v] * p.hx0; hzy = zw[v] * p.hy0; hzz = zw[v] * p.hz0;
                 hdxv = hdx[v]; hdyv = hdy[v]; hdzv = hdz[v];
-                hx = hdxv + hex + hax + hzx;
-                hy = hdyv + hey + hay + hzy;
-                hz = hdzv + hez + haz + hzz;
+                hx = hdxv + hex + hax + hzx + hmx;
+                hy = hdyv + hey + hay + hzy + hmy;
+                hz = hdzv + hez + haz + hzz + hmz;
             }
             hxo[v] = hx; hyo[v] = hy; hzo[v] = hz;
             const T gp = (!UNI && p.alpha_cell) ? (T)(-kGamma) / ((T)1 + al[v] * al[v]) : p.gp_u;
@@ -187,6 +249,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
                 red_e1 += f * ((double)mx[v] * hex + (double)my[v] * hey + (double)mz[v] * hez);
                 red_e2 += f * ((double)mx[v] * hax + (double)my[v] * hay + (double)mz[v] * haz);
                 red_e3 += 2.0 * f * ((double)mx[v] * hzx + (double)my[v] * hzy + (double)mz[v] * hzz);
+                if constexpr (DMI) red_e4 += f * ((double)mx[v] * hmx + (double)my[v] * hmy + (double)mz[v] * hmz);
             }
         }
         if (p.h_out) { LV::st(p.h_out + i, hxo); LV::st(p.h_out + N + i, hyo); LV::st(p.h_out + 2 * N + i, hzo); }
@@ -268,12 +331,13 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
         __shared__ double red[kStageThreads / 32][kNPart];
         const int tid = threadIdx.y * kBX + threadIdx.x;
         const int lane = tid & 31, wid = tid >> 5;
-        double vals[kNPart] = {red_torque, red_e0, red_e1, red_e2, red_e3, red_err, red_nf, 0.0};
+        double vals[kNPart] = {red_torque, red_e0, red_e1, red_e2, red_e3, red_err, red_nf, red_e4};
         vals[R_TORQUE] = warp_max(vals[R_TORQUE]);
         vals[R_ERR] = warp_max(vals[R_ERR]);
         vals[R_NONFINITE] = warp_max(vals[R_NONFINITE]);
 #pragma unroll
         for (int q = R_EDEM; q <= R_EZEE; ++q) vals[q] = warp_sum(vals[q]);
+        vals[R_EDMI] = warp_sum(vals[R_EDMI]);
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < kNPart; ++q) red[wid][q] = vals[q];
@@ -408,15 +472,20 @@ template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t s
     *nblocks = (int)(grid.x * grid.y * grid.z);
     // uniform material needs Ms != 0 too (the Ms = 0 test is compiled away)
     const bool uni = !p.Ms_cell && !p.A_cell && !p.Ku_cell && !p.alpha_cell && !p.zw && p.Ms != (T)0;
-    if (vec == 1) {
-        if (uni) stage_kernel<T, 1, true><<<grid, block, 0, st>>>(p);
-        else stage_kernel<T, 1, false><<<grid, block, 0, st>>>(p);
+    if (p.dmi) {
+        // DMI runs the general (non-uniform) variant
+        if (vec == 1) stage_kernel<T, 1, false, true><<<grid, block, 0, st>>>(p);
+        else if constexpr (sizeof(T) == 4) stage_kernel<T, 4, false, true><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 2, false, true><<<grid, block, 0, st>>>(p);
+    } else if (vec == 1) {
+        if (uni) stage_kernel<T, 1, true, false><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 1, false, false><<<grid, block, 0, st>>>(p);
     } else if constexpr (sizeof(T) == 4) {
-        if (uni) stage_kernel<T, 4, true><<<grid, block, 0, st>>>(p);
-        else stage_kernel<T, 4, false><<<grid, block, 0, st>>>(p);
+        if (uni) stage_kernel<T, 4, true, false><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 4, false, false><<<grid, block, 0, st>>>(p);
     } else {
-        if (uni) stage_kernel<T, 2, true><<<grid, block, 0, st>>>(p);
-        else stage_kernel<T, 2, false><<<grid, block, 0, st>>>(p);
+        if (uni) stage_kernel<T, 2, true, false><<<grid, block, 0, st>>>(p);
+        else stage_kernel<T, 2, false, false><<<grid, block, 0, st>>>(p);
     }
 }
 

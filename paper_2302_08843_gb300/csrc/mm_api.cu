@@ -178,6 +178,9 @@ struct mm_state {
     bool fsal = false;             // K[0] holds the DP45 first stage of the next step
     bool k1_exact = false;         // K[0] = f(m, t) at the current m (RKF45 needs exactly that)
     int precession = 1;            // 0: LLG without the m x h term
+    int dmi_kind = 0;              // mm_dmi_kind
+    double D = 0.0;                // uniform DMI strength (J/m^2), used when D_cell is null
+    void* D_cell = nullptr;        // per-cell DMI strength (real type)
     mm_method relax_method = MM_DP45;
     bool s1_fresh = false;   // S1 holds the x-spectrum of Ms m for the current m (left by the fused RK4 path)
     bool use_fused = true;   // RK4 in FP32 may take the fused stage kernel
@@ -277,6 +280,18 @@ template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, con
     p.hx0 = (T)h[0]; p.hy0 = (T)h[1]; p.hz0 = (T)h[2];
     p.mn = (const T*)s->m;
     p.no_precession = s->precession ? 0 : 1;
+    p.i2dx = (T)(0.5 / s->g.dx); p.i2dy = (T)(0.5 / s->g.dy); p.i2dz = (T)(0.5 / s->g.dz);
+    if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell)) {
+        // DMI vectors e_x, e_y, e_z of the paper's table (e_{-k} = -e_k)
+        static const double vecs[4][9] = {{0, 0, 0, 0, 0, 0, 0, 0, 0},
+                                          {0, 1, 0, -1, 0, 0, 0, 0, 0},     // interface
+                                          {1, 0, 0, 0, 1, 0, 0, 0, 1},      // bulk
+                                          {-1, 0, 0, 0, 1, 0, 0, 0, 0}};    // D2d
+        p.dmi = 1;
+        p.D = (T)s->D;
+        p.D_cell = (const T*)s->D_cell;
+        for (int q = 0; q < 9; ++q) p.dmi_e[q] = (T)vecs[s->dmi_kind][q];
+    }
 }
 
 // demag field of m into s->hd
@@ -336,8 +351,10 @@ mm_status heff_impl(mm_state* s, const void* m, void* h_out, double* E_out, doub
     MM_TRY(run_stage<T>(s, p, reduce));
     if (reduce) {
         MM_TRY(read_scalars(s));
-        if (E_out)
+        if (E_out) {
             for (int q = 0; q < 4; ++q) E_out[q] = s->h_scalars[R_EDEM + q];
+            E_out[4] = s->h_scalars[R_EDMI];
+        }
         if (torque_out) *torque_out = s->h_scalars[R_TORQUE];
         if (s->h_scalars[R_NONFINITE] != 0.0) return fail(MM_ENONFINITE, "non-finite field or torque");
     }
@@ -988,7 +1005,7 @@ void mm_state_destroy(mm_state* s) {
     if (!s) return;
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->st);
-    void** bufs[] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd, &s->S1, &s->S2, &s->tens, &s->Ms_cell,
+    void** bufs[] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd, &s->S1, &s->S2, &s->tens, &s->D_cell, &s->Ms_cell,
                      &s->A_cell, &s->Ku_cell, &s->alpha_cell, &s->axis_tab, reinterpret_cast<void**>(&s->grain),
                      &s->zw, reinterpret_cast<void**>(&s->partials), reinterpret_cast<void**>(&s->scalars),
                      reinterpret_cast<void**>(&s->dev_err)};
@@ -1175,10 +1192,24 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
     if (lambda_n == lambda_np1 || lambda_n == m_n) return fail(MM_EINVAL, "lambda_n must not alias the inputs");
     if (!s->precession) return fail(MM_EINVAL, "the adjoint is written for the LLG right-hand side with precession");
+    if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell))
+        return fail(MM_EINVAL, "the adjoint does not cover the DMI term");
     MM_TRY(ready_for_fields(s));
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)
                               : adjoint_impl<float>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t);
+}
+
+mm_status mm_set_dmi(mm_state* s, mm_dmi_kind kind, double D, const double* D_cell, int on_device) {
+    MM_TRY(check_state(s));
+    if (kind < MM_DMI_NONE || kind > MM_DMI_D2D) return fail(MM_EINVAL, "unknown DMI kind %d", (int)kind);
+    if (!std::isfinite(D)) return fail(MM_EINVAL, "D must be finite");
+    MM_TRY(set_device(s));
+    MM_TRY(upload_real(s, kind == MM_DMI_NONE ? nullptr : D_cell, s->N, on_device, &s->D_cell));
+    s->dmi_kind = kind;
+    s->D = D;
+    s->fsal = s->k1_exact = false;
+    return MM_OK;
 }
 
 mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession) {
