@@ -38,13 +38,9 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, see the design doc
 
 # ----------------------------------------------------------------- models --
 def padded(n):
-    out = []
-    for v in n:
-        p = 1
-        while p < 2 * v:
-            p *= 2
-        out.append(1 if v == 1 else p)
-    return out
+    """The library's padded FFT extents (mm_fft_extent)."""
+    from paper_2302_08843_gb300.binding import padded_extents
+    return list(padded_extents(n))
 
 
 def kernel_bytes(n, s, grains=True, ms_cell=False):

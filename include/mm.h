@@ -282,6 +282,13 @@ mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession
  * spins < 1. */
 mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins);
 
+/* Host-only helper (no GPU): the padded FFT extent the library uses along an
+ * axis of n cells (Sec. 4.4 zero padding, P >= 2n): 1 for n = 1, otherwise the
+ * smallest length >= 2n among the powers of two up to 4096 and the 5-smooth
+ * lengths 100, 200, 400 and 800, which the mixed-radix passes transform.
+ * 0 for n < 1. */
+int mm_fft_extent(int n);
+
 /* Host-only helper (no GPU): the real-space demag tensor this library builds
  * (Sec. 4.4, same rule as mm_demag_setup) for every cell offset, as
  * 6 x (2nx-1) x (2ny-1) x (2nz-1) doubles, components (xx, xy, xz, yy, yz, zz),

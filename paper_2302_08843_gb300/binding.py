@@ -27,7 +27,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
-           "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi")
+           "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent")
 
 
 class MMError(RuntimeError):
@@ -97,6 +97,7 @@ def lib():
         "mm_selftest_wait_timeout": (i, [vp, ctypes.c_uint]),
         "mm_set_llg_options": (i, [vp, i, i]),
         "mm_set_dmi": (i, [vp, i, d, vp, i]),
+        "mm_fft_extent": (i, [i]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -138,17 +139,9 @@ def demag_tensor_host(n, dx, p=20):
 
 
 def padded_extents(n):
-    """Padded FFT extent per axis: next power of two >= 2n, 1 for a single cell."""
-    out = []
-    for v in n:
-        if v == 1:
-            out.append(1)
-        else:
-            p = 1
-            while p < 2 * v:
-                p *= 2
-            out.append(p)
-    return tuple(out)
+    """Padded FFT extent per axis (mm_fft_extent): 1 for a single cell, else the
+    smallest supported length >= 2n (powers of two and 100, 200, 400, 800)."""
+    return tuple(int(lib().mm_fft_extent(int(v))) for v in n)
 
 
 def demag_spectrum_host(n, dx, p=20):

@@ -33,6 +33,12 @@ template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
 // translation unit that runs FFTs owns a copy and an upload function).
 static __device__ double2 g_tw64[kMaxFft];
 static __device__ float2 g_tw32[kMaxFft];
+// W5[m] = exp(-2 pi i m / kTw5): twiddles of the 5-smooth lengths (all divide kTw5)
+constexpr int kTw5 = 3200;
+static __device__ double2 g_tw5_64[kTw5];
+static __device__ float2 g_tw5_32[kTw5];
+
+__host__ __device__ constexpr bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 template <typename T> struct Tw;
 template <> struct Tw<float> {
@@ -41,6 +47,20 @@ template <> struct Tw<float> {
 template <> struct Tw<double> {
     static __device__ __forceinline__ double2 get(int m) { return __ldg(&g_tw64[m]); }
 };
+
+template <typename T> struct Tw5;
+template <> struct Tw5<float> {
+    static __device__ __forceinline__ float2 get(int m) { return __ldg(&g_tw5_32[m]); }
+};
+template <> struct Tw5<double> {
+    static __device__ __forceinline__ double2 get(int m) { return __ldg(&g_tw5_64[m]); }
+};
+// exp(DIR * 2 pi i m / kTw5), 0 <= m < kTw5
+template <typename T, int DIR> __device__ __forceinline__ typename Cplx<T>::type twiddle5(int m) {
+    typename Cplx<T>::type w = Tw5<T>::get(m);
+    if (DIR > 0) w.y = -w.y;
+    return w;
+}
 
 // exp(DIR * 2 pi i k / L) for 0 <= k < L (L a power of two <= kMaxFft)
 template <typename T, int L, int DIR> __device__ __forceinline__ typename Cplx<T>::type twiddle(int k) {
@@ -109,6 +129,28 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8_half(C* a) {
 }
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// DFT5 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 5), from the pairs
+// a1 +- a4, a2 +- a3 and the cosines and sines of 2 pi / 5 and 4 pi / 5
+template <int DIR, typename C> __device__ __forceinline__ void dft5(C& a0, C& a1, C& a2, C& a3, C& a4) {
+    using T = decltype(C::x);
+    constexpr T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    constexpr T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+    const C p1 = cadd(a1, a4), m1 = csub(a1, a4), p2 = cadd(a2, a3), m2 = csub(a2, a3);
+    const C t1 = mk<C>(a0.x + c1 * p1.x + c2 * p2.x, a0.y + c1 * p1.y + c2 * p2.y);
+    const C t2 = mk<C>(a0.x + c2 * p1.x + c1 * p2.x, a0.y + c2 * p1.y + c1 * p2.y);
+    // u = s1 m1 + s2 m2, w = s2 m1 - s1 m2: X1 = t1 + DIR i u, X4 = t1 - DIR i u,
+    // X2 = t2 + DIR i w, X3 = t2 - DIR i w
+    const C u = mk<C>(s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y);
+    const C w = mk<C>(s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y);
+    const C iu = DIR < 0 ? mk<C>(u.y, -u.x) : mk<C>(-u.y, u.x);     // DIR i u
+    const C iw = DIR < 0 ? mk<C>(w.y, -w.x) : mk<C>(-w.y, w.x);
+    a0 = mk<C>(a0.x + p1.x + p2.x, a0.y + p1.y + p2.y);
+    a1 = cadd(t1, iu);
+    a4 = csub(t1, iu);
+    a2 = cadd(t2, iw);
+    a3 = csub(t2, iw);
+}
 
 // cos and sin of pi k / 8, k = 0..15
 __host__ __device__ constexpr double c16(int k) {

@@ -11,6 +11,20 @@
 
 namespace mm {
 
+// Padded FFT extent of an axis of n cells: 1 for one cell, otherwise the
+// smallest length >= 2n among the powers of two and the 5-smooth lengths the
+// FFT engines support (100, 200, 400, 800).
+inline int fft_extent(int n) {
+    if (n <= 1) return 1;
+    const int t = 2 * n;
+    int best = 1;
+    while (best < t) best <<= 1;
+    const int mixed[4] = {100, 200, 400, 800};
+    for (int L : mixed)
+        if (L >= t && L < best) best = L;
+    return best;
+}
+
 struct DemagDims {
     int nx, ny, nz;      // cells
     int LX, LY, LZ;      // padded FFT extents
@@ -117,7 +131,7 @@ template <typename T> void launch_renorm_copy(const T* src, T* dst, long N, cuda
 template <typename T> void launch_combine(const T* mn, const T* const* kin, const double* kc, int nk, double dt,
                                           T* out, long N, cudaStream_t st);
 // copy the host-built twiddle table into the FFT kernels' device table (current device)
-cudaError_t upload_twiddles(const double2* w64, const float2* w32);
+cudaError_t upload_twiddles(const double2* w64, const float2* w32, const double2* w5_64, const float2* w5_32);
 // build (once, in static host storage) and upload the twiddle table to device dev, which
 // must be current; a no-op after the first success on that device
 cudaError_t ensure_twiddles_on(int dev);

@@ -30,10 +30,12 @@
 
 namespace mm {
 
-cudaError_t upload_twiddles(const double2* w64, const float2* w32) {
+cudaError_t upload_twiddles(const double2* w64, const float2* w32, const double2* w5_64, const float2* w5_32) {
     cudaError_t e = cudaMemcpyToSymbol(g_tw64, w64, sizeof(double2) * kMaxFft);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(g_tw32, w32, sizeof(float2) * kMaxFft);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw32, w32, sizeof(float2) * kMaxFft);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw5_64, w5_64, sizeof(double2) * kTw5);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw5_32, w5_32, sizeof(float2) * kTw5);
+    return e;
 }
 
 // ------------------------------------------------------------------ P1 ----
@@ -104,7 +106,7 @@ p1_x_forward(DemagDims d, const T* __restrict__ m, const T* __restrict__ Ms_cell
         const int l = idx / KXn, k = idx - l * KXn;
         const long ra = ra_s[l], rb = rb_s[l];
         const C zk = s[k * LS + l];
-        const C zm = s[((LX - k) & (LX - 1)) * LS + l];
+        const C zm = s[(k == 0 ? 0 : LX - k) * LS + l];     // mirror index, any even LX
         if (ra >= 0) S1[ra * d.KXS + k] = mk<C>(half * (zk.x + zm.x), half * (zk.y - zm.y));
         if (rb >= 0) S1[rb * d.KXS + k] = mk<C>(half * (zk.y + zm.y), half * (zm.x - zk.x));
     }
@@ -1311,7 +1313,9 @@ template <typename T, int L> static void launch_p3(const DemagDims& d, typename 
     const int kyi = 2 * (d.LY / 2 + 1);
     dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G, d.nb);
     if constexpr (sizeof(T) == 4 && L <= 256) {
-        if (d.nb == 1 && launch_p3_tma<L>(d, S2, tens, st)) return;
+        if constexpr (is_pow2(L)) {
+            if (d.nb == 1 && launch_p3_tma<L>(d, S2, tens, st)) return;
+        }
         // 128-thread CTAs: three fit per SM at up to 170 registers per thread
         constexpr int G3 = (B * tpl_of<T, L>() >= 128) ? 1 : 128 / (B * tpl_of<T, L>());
         dim3 grid3((d.KX + B - 1) / B, (kyi + G3 - 1) / G3, d.nb);
@@ -1329,7 +1333,7 @@ template <typename T, int L> static void launch_p3(const DemagDims& d, typename 
 
 template <typename T, int L, int DIR> static void launch_y(const DemagDims& d, const typename Cplx<T>::type* in,
                                                            typename Cplx<T>::type* out, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && L >= 16) {
+    if constexpr (sizeof(T) == 4 && L >= 16 && is_pow2(L)) {
         if (launch_py_tma<L, DIR>(d, in, out, st)) return;
     }
     launch_py<T, L, DIR>(d, in, out, st);
@@ -1337,7 +1341,7 @@ template <typename T, int L, int DIR> static void launch_y(const DemagDims& d, c
 
 template <typename T, int L> static void launch_x_fwd(const DemagDims& d, const T* m, const T* Ms_cell, T Ms,
                                                       typename Cplx<T>::type* S1, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && L >= 16) {
+    if constexpr (sizeof(T) == 4 && L >= 16 && is_pow2(L)) {
         if (launch_p1_tma<L>(d, m, Ms_cell, Ms, S1, st)) return;
     }
     launch_p1<T, L>(d, m, Ms_cell, Ms, S1, st);
@@ -1345,7 +1349,7 @@ template <typename T, int L> static void launch_x_fwd(const DemagDims& d, const 
 
 template <typename T, int L> static void launch_x_inv(const DemagDims& d, const typename Cplx<T>::type* S1, T* h,
                                                       cudaStream_t st) {
-    if constexpr (sizeof(T) == 4 && L >= 16) {
+    if constexpr (sizeof(T) == 4 && L >= 16 && is_pow2(L)) {
         if (launch_p5_tma<L>(d, S1, h, st)) return;
     }
     launch_p5<T, L>(d, S1, h, st);
@@ -1357,7 +1361,7 @@ constexpr int kK5Rows = 2, kK5Slots = 1, kK5Pad = 0, kK5MinBlocks = 8;
 
 template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st) {
     constexpr int TY = kK5Rows;
-    if constexpr (L < 16) {
+    if constexpr (L < 16 || !is_pow2(L)) {
         return false;
     } else {
         if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
@@ -1404,6 +1408,10 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         case 1024: { constexpr int L_ = 1024; CALL; } break; \
         case 2048: { constexpr int L_ = 2048; CALL; } break; \
         case 4096: { constexpr int L_ = 4096; CALL; } break; \
+        case 100: { constexpr int L_ = 100; CALL; } break;   \
+        case 200: { constexpr int L_ = 200; CALL; } break;   \
+        case 400: { constexpr int L_ = 400; CALL; } break;   \
+        case 800: { constexpr int L_ = 800; CALL; } break;   \
         default: break;                     \
     }
 
@@ -1468,7 +1476,7 @@ bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cu
 }
 
 bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
-    if (!d.err || d.LX < 16 || d.LX > 4096 || d.nx % 2 != 0) return false;
+    if (!d.err || d.LX < 16 || d.LX > 4096 || !is_pow2(d.LX) || d.nx % 2 != 0) return false;
     if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f) return false;
     const int threads = (3 * kK5Rows / 2) * (d.LX / 16);
     return threads <= 1024;

@@ -238,9 +238,93 @@ struct FftLine16 {
     }
 };
 
-// engine choice: radix 16 for FP32 lines of 16+ points, radix 8 otherwise
+// ------------------------------------------------------------------------
+// Mixed-radix engine for the 5-smooth lengths L = 5^b 2^a (L divides kTw5):
+// radix-5 passes, then radix-4 passes and at most one radix-2 pass, Stockham
+// ordering.  Every pass keeps the line in shared memory: a thread reads its
+// butterflies' inputs (stride L/R), applies the twiddles W_{Ns R}^(q k),
+// transforms them and writes the outputs to their autosorted places.  The
+// register layout at entry and exit and the calling convention are those of
+// FftLine (register r of thread j holds element j + r TPL), so the same
+// kernels drive it; TPL is the largest thread count that divides L/R for
+// every radix R of the plan.
+__host__ __device__ constexpr int m5_fives(int L) { return L % 5 ? 0 : 1 + m5_fives(L / 5); }
+__host__ __device__ constexpr int m5_pow5(int b) { return b == 0 ? 1 : 5 * m5_pow5(b - 1); }
+__host__ __device__ constexpr int m5_twos(int L) { return ilog2(L / m5_pow5(m5_fives(L))); }
+__host__ __device__ constexpr int m5_npass(int L) {
+    return m5_fives(L) + m5_twos(L) / 2 + m5_twos(L) % 2;
+}
+__host__ __device__ constexpr int m5_radix(int L, int p) {
+    return p < m5_fives(L) ? 5 : (p < m5_fives(L) + m5_twos(L) / 2 ? 4 : 2);
+}
+__host__ __device__ constexpr int m5_gcd(int a, int b) { return b == 0 ? a : m5_gcd(b, a % b); }
+__host__ __device__ constexpr int m5_tpl(int L, int p = 0) {
+    return p == m5_npass(L) - 1 ? L / m5_radix(L, p) : m5_gcd(L / m5_radix(L, p), m5_tpl(L, p + 1));
+}
+
 template <typename T, int L, int DIR, bool ZIN>
-using Fft = typename std::conditional<(sizeof(T) == 4 && L >= 16), FftLine16<T, L, DIR, ZIN>,
-                                      FftLine<T, L, DIR, ZIN>>::type;
+struct FftMixed {
+    using C = typename Cplx<T>::type;
+    static_assert(kTw5 % L == 0, "5-smooth lengths must divide the twiddle table");
+    static constexpr int NP = m5_npass(L);
+    static constexpr int TPL = m5_tpl(L);
+    static constexpr int NR = L / TPL;
+    static constexpr int NTW = 0;
+    static_assert(NR % 2 == 0, "the zero-padded half must be whole registers");
+
+    static __device__ __forceinline__ int in_index(int j, int r) { return j + r * TPL; }
+    static __host__ __device__ constexpr bool in_live(int r) { return !ZIN || r < NR / 2; }
+    static __device__ void tw_build(C*, int, int) {}
+
+    template <int P, int NS>
+    static __device__ __forceinline__ void pass(C* s, int LS, int j) {
+        constexpr int R = m5_radix(L, P);
+        constexpr int NB = L / (R * TPL);    // butterflies per thread
+        C a[NB][R];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const int b = j + t * TPL;
+            const int k = b % NS;
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[t][q] = s[(b + q * (L / R)) * LS];
+            if (NS > 1) {
+#pragma unroll
+                for (int q = 1; q < R; ++q) a[t][q] = cmul(a[t][q], twiddle5<T, DIR>(q * k * (kTw5 / (NS * R))));
+            }
+            if constexpr (R == 5) dft5<DIR>(a[t][0], a[t][1], a[t][2], a[t][3], a[t][4]);
+            else if constexpr (R == 4) dft4<DIR>(a[t][0], a[t][1], a[t][2], a[t][3]);
+            else dft2<DIR>(a[t][0], a[t][1]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const int b = j + t * TPL;
+            const int k = b % NS;
+            const int base = (b - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[(base + q * NS) * LS] = a[t][q];
+        }
+        __syncthreads();
+        if constexpr (P + 1 < NP) pass<P + 1, NS * R>(s, LS, j);
+    }
+
+    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j, const C* = nullptr) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s[(j + r * TPL) * LS] = v[r];
+        __syncthreads();
+        pass<0, 1>(s, LS, j);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = s[(j + r * TPL) * LS];
+    }
+};
+
+// engine choice: the mixed-radix engine for 5-smooth lengths, radix 16 for
+// FP32 power-of-two lines of 16+ points, radix 8 otherwise
+template <typename T, int L, int DIR, bool ZIN>
+using Fft = typename std::conditional<
+    !is_pow2(L), FftMixed<T, L, DIR, ZIN>,
+    typename std::conditional<(sizeof(T) == 4 && L >= 16), FftLine16<T, L, DIR, ZIN>,
+                              FftLine<T, L, DIR, ZIN>>::type>::type;
 
 }  // namespace mm

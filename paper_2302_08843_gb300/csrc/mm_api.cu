@@ -52,16 +52,13 @@ mm_status fail(mm_status st, const char* fmt, ...) {
         if (s_ != MM_OK) return s_;      \
     } while (0)
 
-int next_pow2(int v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
 
 std::mutex g_tw_mu;
 bool g_tw_done[128] = {false};
 double2 g_tw_host64[kMaxFft];    // static host staging: the upload allocates nothing
 float2 g_tw_host32[kMaxFft];
+double2 g_tw5_host64[kTw5];
+float2 g_tw5_host32[kTw5];
 
 }  // namespace
 
@@ -81,9 +78,15 @@ cudaError_t ensure_twiddles_on(int dev) {
             g_tw_host64[i] = make_double2(c, sn);
             g_tw_host32[i] = make_float2((float)c, (float)sn);
         }
+        for (int i = 0; i < kTw5; ++i) {
+            double c, sn;
+            twiddle_entry(kTw5, i, &c, &sn);
+            g_tw5_host64[i] = make_double2(c, sn);
+            g_tw5_host32[i] = make_float2((float)c, (float)sn);
+        }
         built = true;
     }
-    cudaError_t e = upload_twiddles(g_tw_host64, g_tw_host32);
+    cudaError_t e = upload_twiddles(g_tw_host64, g_tw_host32, g_tw5_host64, g_tw5_host32);
     if (e == cudaSuccess) g_tw_done[dev] = true;
     return e;
 }
@@ -774,9 +777,7 @@ struct mm_batch {
 namespace {
 
 size_t batch_bytes(const mm_grid* g, mm_precision prec, int cap, int* LXo, int* LYo, int* LZo, int* KXSo) {
-    const int LX = g->nx == 1 ? 1 : next_pow2(2 * g->nx);
-    const int LY = g->ny == 1 ? 1 : next_pow2(2 * g->ny);
-    const int LZ = g->nz == 1 ? 1 : next_pow2(2 * g->nz);
+    const int LX = fft_extent(g->nx), LY = fft_extent(g->ny), LZ = fft_extent(g->nz);
     const size_t rsz = prec == MM_FP64 ? 8 : 4, csz = 2 * rsz;
     const int align = (int)(128 / csz);
     const int KX = LX / 2 + 1, KXS = (KX + align - 1) / align * align;
@@ -955,9 +956,7 @@ mm_status mm_state_create(const mm_grid* grid, mm_precision precision, void* cud
     if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0)) return fail(MM_EINVAL, "cell sizes must be > 0");
     if ((double)grid->nx * grid->ny * grid->nz >= 2147483648.0) return fail(MM_EINVAL, "too many cells");
     if (precision != MM_FP64 && precision != MM_FP32_FIELDS) return fail(MM_EINVAL, "bad precision");
-    const int LX = grid->nx == 1 ? 1 : next_pow2(2 * grid->nx);
-    const int LY = grid->ny == 1 ? 1 : next_pow2(2 * grid->ny);
-    const int LZ = grid->nz == 1 ? 1 : next_pow2(2 * grid->nz);
+    const int LX = fft_extent(grid->nx), LY = fft_extent(grid->ny), LZ = fft_extent(grid->nz);
     if (LX > kMaxFft || LY > kMaxFft || LZ > kMaxFft)
         return fail(MM_EINVAL, "padded FFT extent above %d (grid %d x %d x %d)", kMaxFft, grid->nx, grid->ny,
                     grid->nz);
@@ -1232,6 +1231,8 @@ mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins) {
     return MM_OK;
 }
 
+int mm_fft_extent(int n) { return n < 1 ? 0 : fft_extent(n); }
+
 size_t mm_batch_footprint(const mm_grid* grid, mm_precision precision, int capacity) {
     if (!grid || capacity < 1) return 0;
     return batch_bytes(grid, precision, capacity, nullptr, nullptr, nullptr, nullptr);
@@ -1453,8 +1454,7 @@ mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out)
         return fail(MM_EINVAL, "bad grid");
     const int n[3] = {grid->nx, grid->ny, grid->nz};
     const double dd[3] = {grid->dx, grid->dy, grid->dz};
-    const int P[3] = {grid->nx == 1 ? 1 : next_pow2(2 * grid->nx), grid->ny == 1 ? 1 : next_pow2(2 * grid->ny),
-                      grid->nz == 1 ? 1 : next_pow2(2 * grid->nz)};
+    const int P[3] = {fft_extent(grid->nx), fft_extent(grid->ny), fft_extent(grid->nz)};
     if (P[0] > kMaxFft || P[1] > kMaxFft || P[2] > kMaxFft) return fail(MM_EINVAL, "padded extent too large");
     std::vector<double> spec;
     tensor_spectrum(n, dd, p_newell, P, P[0] / 2 + 1, spec);

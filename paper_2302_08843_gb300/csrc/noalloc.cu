@@ -28,12 +28,6 @@ std::mutex g_mu;
 void* g_scratch_ptr[128] = {nullptr};   // device address of g_noalloc_scratch per device
 thread_local char g_msg[256];
 
-int next_pow2(int v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
 mm_status err(mm_status st, const char* what) {
     mm::set_last_error(what);
     return st;
@@ -54,9 +48,7 @@ extern "C" mm_status mm_demag_noalloc(const mm_grid* grid, mm_precision precisio
     if (precision != MM_FP64 && precision != MM_FP32_FIELDS) return err(MM_EINVAL, "mm_demag_noalloc: bad precision");
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || (double)grid->nx * grid->ny * grid->nz >= 2147483648.0)
         return err(MM_EINVAL, "mm_demag_noalloc: grid sizes must be >= 1");
-    const int LX = grid->nx == 1 ? 1 : next_pow2(2 * grid->nx);
-    const int LY = grid->ny == 1 ? 1 : next_pow2(2 * grid->ny);
-    const int LZ = grid->nz == 1 ? 1 : next_pow2(2 * grid->nz);
+    const int LX = fft_extent(grid->nx), LY = fft_extent(grid->ny), LZ = fft_extent(grid->nz);
     if (LX > kMaxFft || LY > kMaxFft || LZ > kMaxFft)
         return err(MM_EINVAL, "mm_demag_noalloc: padded FFT extent above 4096");
     const int KX = LX / 2 + 1;

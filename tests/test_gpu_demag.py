@@ -1,7 +1,8 @@
 """GPU parity of the demag field (Sec. 4.4): the five FFT passes of libmm.so
 against the oracle's convolution, element by element, FP64 and FP32, on grids
-that cover one cell, 1-D and 2-D lines, ragged (non power of two) extents that
-pad beyond 2n, several CTA tiles with ragged tails, and the largest padded
+that cover one cell, 1-D and 2-D lines, ragged extents that pad beyond 2n,
+every 5-smooth padded length of the mixed-radix passes (100, 200, 400, 800,
+on each axis), several CTA tiles with ragged tails, and the largest padded
 extent (4096)."""
 import numpy as np
 import pytest
@@ -25,7 +26,19 @@ GRIDS = [
     ((5, 70, 3), (2e-9, 2e-9, 2e-9)),
     ((6, 5, 40), (2e-9, 2e-9, 2e-9)),
     ((2048, 2, 1), (1e-9, 1e-9, 1e-9)),
+    ((200, 6, 2), (2e-9, 2e-9, 2e-9)),          # x padded to 400
+    ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 800
+    ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 400
+    ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 100
 ]
+
+
+def test_padded_extents_rule():
+    from paper_2302_08843_gb300.binding import padded_extents
+    assert padded_extents((1, 2, 3)) == (1, 4, 8)
+    assert padded_extents((50, 64, 100)) == (100, 128, 200)
+    assert padded_extents((150, 200, 300)) == (400, 400, 800)
+    assert padded_extents((401, 2048, 33)) == (1024, 4096, 100)
 
 
 def _m(n, seed):
