@@ -33,6 +33,9 @@ struct DemagDims {
     int* err = nullptr;  // device error word for bounded-wait failures; null: no TMA kernels
     int nb = 1;          // grids of this shape stacked as a leading batch dimension
     const void* Ms_b = nullptr;   // per-grid Ms (nb values of the real type) or null
+    // 2-D grids: the z-pass kernels run along y (nz' = ny, Pz' = Py); the
+    // odd components' mirror signs then come from the transformed axis
+    int yz_swap = 0;
 };
 
 // CUDA-event timing of kernel launches on a stream (inactive unless enabled).

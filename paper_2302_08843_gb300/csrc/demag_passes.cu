@@ -752,8 +752,8 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
         if (valid) {
             const T* tp = tens + ((long)kzf * KY2 + p) * d.KXS + kx;
             txx = __ldg(tp);
-            txy = sy * __ldg(tp + tcomp);
-            txz = sz * __ldg(tp + 2 * tcomp);
+            txy = (d.yz_swap ? sz : sy) * __ldg(tp + tcomp);
+            txz = (d.yz_swap ? sy : sz) * __ldg(tp + 2 * tcomp);
             tyy = __ldg(tp + 3 * tcomp);
             tyz = sy * sz * __ldg(tp + 4 * tcomp);
             tzz = __ldg(tp + 5 * tcomp);
@@ -836,8 +836,8 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
         if (valid) {
             const T* tp = tens + ((long)kzf * KY2 + p) * d.KXS + kx;
             txx = __ldg(tp);
-            txy = sy * __ldg(tp + tcomp);
-            txz = sz * __ldg(tp + 2 * tcomp);
+            txy = (d.yz_swap ? sz : sy) * __ldg(tp + tcomp);
+            txz = (d.yz_swap ? sy : sz) * __ldg(tp + 2 * tcomp);
             tyy = __ldg(tp + 3 * tcomp);
             tyz = sy * sz * __ldg(tp + 4 * tcomp);
             tzz = __ldg(tp + 5 * tcomp);
@@ -982,8 +982,8 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
             const int kzf = (2 * kz <= LZ) ? kz : LZ - kz;
             const float sz = (2 * kz <= LZ) ? 1.f : -1.f;
             const float txx = ts[(0 * KZ2 + kzf) * B + line];
-            const float txy = sy * ts[(1 * KZ2 + kzf) * B + line];
-            const float txz = sz * ts[(2 * KZ2 + kzf) * B + line];
+            const float txy = (d.yz_swap ? sz : sy) * ts[(1 * KZ2 + kzf) * B + line];
+            const float txz = (d.yz_swap ? sy : sz) * ts[(2 * KZ2 + kzf) * B + line];
             const float tyy = ts[(3 * KZ2 + kzf) * B + line];
             const float tyz = sy * sz * ts[(4 * KZ2 + kzf) * B + line];
             const float tzz = ts[(5 * KZ2 + kzf) * B + line];
@@ -1415,15 +1415,21 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         default: break;                     \
     }
 
+// P2 .. P4: S1 -> S1 through the tensor multiply.  A 2-D grid (nz = 1, Py <= 256)
+// runs the z-pass kernel along y in place on S1 instead (one pass, no S2).
 template <typename T>
-void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typename Cplx<T>::type* S1,
-                 typename Cplx<T>::type* S2, const T* tens, T* h, cudaStream_t st, KernelTimer* tm) {
+static void yzy(const DemagDims& d, typename Cplx<T>::type* S1, typename Cplx<T>::type* S2, const T* tens,
+                cudaStream_t st, KernelTimer* tm) {
     using C = typename Cplx<T>::type;
-    // With ny == 1 the y passes are the identity and S2 aliases S1.
+    if (d.nz == 1 && d.LY > 1 && d.LY <= 256) {
+        DemagDims d2 = d;
+        d2.ny = 1; d2.nz = d.ny; d2.LY = 1; d2.LZ = d.LY; d2.yz_swap = 1;
+        tm->begin(st, "p3_z_conv");
+        MM_DISPATCH_L(d2.LZ, (launch_p3<T, L_>(d2, S1, tens, st)));
+        tm->end(st);
+        return;
+    }
     C* S2e = d.LY == 1 ? S1 : S2;
-    tm->begin(st, "p1_x_forward");
-    MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
-    tm->end(st);
     if (d.LY > 1) {
         tm->begin(st, "p2_y_forward");
         MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
@@ -1437,6 +1443,16 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
         MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
         tm->end(st);
     }
+}
+
+template <typename T>
+void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typename Cplx<T>::type* S1,
+                 typename Cplx<T>::type* S2, const T* tens, T* h, cudaStream_t st, KernelTimer* tm) {
+    // With ny == 1 the y passes are the identity and S2 aliases S1.
+    tm->begin(st, "p1_x_forward");
+    MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
+    tm->end(st);
+    yzy<T>(d, S1, S2, tens, st, tm);
     tm->begin(st, "p5_x_inverse");
     MM_DISPATCH_L(d.LX, (launch_x_inv<T, L_>(d, S1, h, st)));
     tm->end(st);
@@ -1445,26 +1461,12 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
 template <typename T>
 void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
                  typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm) {
-    using C = typename Cplx<T>::type;
-    C* S2e = d.LY == 1 ? S1 : S2;
     if (need_p1) {
         tm->begin(st, "p1_x_forward");
         MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
         tm->end(st);
     }
-    if (d.LY > 1) {
-        tm->begin(st, "p2_y_forward");
-        MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
-        tm->end(st);
-    }
-    tm->begin(st, "p3_z_conv");
-    MM_DISPATCH_L(d.LZ, (launch_p3<T, L_>(d, S2e, tens, st)));
-    tm->end(st);
-    if (d.LY > 1) {
-        tm->begin(st, "p4_y_inverse");
-        MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
-        tm->end(st);
-    }
+    yzy<T>(d, S1, S2, tens, st, tm);
 }
 
 bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st, KernelTimer* tm) {
