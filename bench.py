@@ -408,6 +408,72 @@ def b1_cufft_measure(torch, w, steps, warmup, s32):
                     "PyTorch kernels, FP32"}
 
 
+def workloads_measure(torch):
+    """Time to solution of the paper-shaped configurations beside the bulk one
+    (wall time with the device synchronised): plain FP64 (32x32x4, 200 RK4
+    steps), the thin film (512x128x1, DP45 with rtol 1e-5 to 1 ns, FP64 and
+    FP32 fields) and the inverse design (128x128x1, 2000 FP32 RK4 steps and the
+    gradient of the time-averaged output m_y by the checkpointed adjoint)."""
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.autodiff import rk4_observable
+    from paper_2302_08843_gb300.binding import State, setup_workload
+    from paper_2302_08843_gb300.workloads import to_soa
+    out = {}
+    w = W.plain_fp64()
+    s = setup_workload(w, "fp64")
+    s.step(w.dt, 0.0, "rk4")
+    s.set_m(to_soa(w.m0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t = 0.0
+    for _ in range(w.steps):
+        t, _ = s.step(w.dt, t, "rk4")
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["plain_fp64_32x32x4_rk4_200"] = {"seconds": round(el, 4), "steps": w.steps}
+    s.close()
+    w = W.thin_film()
+    for prec in ("fp64", "fp32"):
+        s = setup_workload(w, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, dt, steps = 0.0, 1e-13, 0
+        while t < 1e-9:
+            t, dt = s.step(min(dt, 1e-9 - t), t, "dp45", w.extra["rtol"])
+            steps += 1
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out["thin_film_512x128x1_dp45_1ns_" + prec] = {"seconds": round(el, 3), "accepted_steps": steps,
+                                                        "cell_steps_per_s": w.ncells * steps / el}
+        s.close()
+    w = W.inverse_design()
+    s = State(w.n, w.dx, "fp32")
+    s.set_zeeman(fn=w.h_ext, weight=to_soa(w.h_ext_weight))
+    s.demag_setup(20)
+    m0 = torch.from_numpy(to_soa(w.m0)).float().cuda()
+    weight = np.zeros(w.n + (3,))
+    (x0, x1), (y0, y1) = w.extra["out_box"]
+    weight[x0:x1, y0:y1, :, 1] = 1.0 / ((x1 - x0) * (y1 - y0))
+    weight = torch.from_numpy(to_soa(weight)).float().cuda()
+    wt = torch.tensor(to_soa(w.extra["w"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    obs = rk4_observable(torch.sigmoid(wt) * w.extra["Ms0"], s, m0, weight, w.dt, w.steps, 100,
+                         dict(A=w.A, alpha=w.alpha))
+    loss = obs.mean()
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    loss.backward()
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    out["inverse_design_128x128x1_fp32_2000_steps"] = {"forward_seconds": round(fwd, 3),
+                                                       "forward_and_gradient_seconds": round(total, 3),
+                                                       "checkpoint_every": 100}
+    s.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def serve_measure(torch, n_requests, dist=None, rank=0, ws=1):
     """The served stream (Poisson arrivals, mean 2 ms; five grid shapes; FP32
     batched relax under a 40 GB footprint cap): p50/p99 latency and
@@ -535,6 +601,7 @@ def run_ours(args):
     serving = None
     if args.serve_requests > 0 and not args.nz:
         serving = serve_measure(torch, args.serve_requests, dist, rank, ws)
+    other = workloads_measure(torch) if (rank == 0 and not args.nz and not args.no_workloads) else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -614,6 +681,8 @@ def run_ours(args):
         out["b1_cufft"] = dict(r32["b1"], ours_over_b1=round(value / r32["b1"]["value"], 3))
     if serving is not None:
         out["serving"] = serving
+    if other is not None:
+        out["workloads"] = other
     if cpu is not None:
         out["cpu_baseline"] = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stage of the FP64 oracle on the "
                                                   "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")
@@ -672,6 +741,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-b1", action="store_true", help="skip the cuFFT + elementwise comparison baseline")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other configurations' timings")
     ap.add_argument("--nz", type=int, default=0,
                     help="profiling case: the bulk workload cropped to nz planes (the printed line is not a bench "
                          "result)")

@@ -1081,8 +1081,10 @@ template <typename T, int L> constexpr int g_of() {
     return (b_of<T, L>() * tpl_of<T, L>() >= 256) ? 1 : 256 / (b_of<T, L>() * tpl_of<T, L>());
 }
 
+// raise a kernel's dynamic shared-memory limit when the request comes near the
+// 48 KB default (kernels may also hold a little static shared memory)
 template <typename K> static void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T, int L> static void launch_p1(const DemagDims& d, const T* m, const T* Ms_cell, T Ms,

@@ -30,6 +30,8 @@ GRIDS = [
     ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 800
     ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 400
     ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 100
+    ((512, 3, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 1024
+    ((1024, 2, 1), (2e-9, 2e-9, 2e-9)),         # x padded to 2048
 ]
 
 
