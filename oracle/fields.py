@@ -41,15 +41,16 @@ def _inv_ms(Ms, shape):
     return out
 
 
-def exchange_field(m, Ms, A, dx):
+def exchange_field(m, Ms, A, dx, axes=(0, 1, 2)):
     """h_i = 2/(mu0 Ms_i) sum_{k=+-x,+-y,+-z} 2/D_k^2 A_{i+k} A_i/(A_{i+k}+A_i) (m_{i+k} - m_i).
 
     A link whose harmonic-mean denominator A_i + A_{i+k} is 0 carries no
-    weight (reading: both cells have A = 0)."""
+    weight (reading: both cells have A = 0).  ``axes`` limits the sum to
+    the links along the given axes."""
     shape = m.shape[:3]
     A = _grid(A, shape)
     h = np.zeros_like(m)
-    for ax in range(3):
+    for ax in axes:
         d2 = float(dx[ax]) ** 2
         n = shape[ax]
         if n < 2:
@@ -88,15 +89,20 @@ def zeeman_field(h_ext, shape, weight=None):
 
 
 def linear_energy(m, h, Ms, V):
-    """Eq. linear_energy_discrete: E = -1/2 mu0 V sum_i Ms_i m_i . h_i."""
+    """Eq. linear_energy_discrete: E = -1/2 mu0 V sum_i Ms_i m_i . h_i
+    (V a scalar, or per cell: an array broadcastable to the grid)."""
     Ms = _grid(Ms, m.shape[:3])
-    return -0.5 * MU0 * V * float(np.sum(Ms * np.sum(m * h, axis=-1)))
+    if np.ndim(V) == 0:
+        return -0.5 * MU0 * V * float(np.sum(Ms * np.sum(m * h, axis=-1)))
+    return -0.5 * MU0 * float(np.sum(_grid(V, m.shape[:3]) * Ms * np.sum(m * h, axis=-1)))
 
 
 def zeeman_energy(m, h, Ms, V):
-    """E = -mu0 V sum_i Ms_i m_i . h_i."""
+    """E = -mu0 V sum_i Ms_i m_i . h_i (V as in linear_energy)."""
     Ms = _grid(Ms, m.shape[:3])
-    return -MU0 * V * float(np.sum(Ms * np.sum(m * h, axis=-1)))
+    if np.ndim(V) == 0:
+        return -MU0 * V * float(np.sum(Ms * np.sum(m * h, axis=-1)))
+    return -MU0 * float(np.sum(_grid(V, m.shape[:3]) * Ms * np.sum(m * h, axis=-1)))
 
 
 # DMI vectors (e_x, e_y, e_z) of the paper's table of DMI types

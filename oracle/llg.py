@@ -39,6 +39,7 @@ from .constants import GAMMA
 from .demag import demag_fft, magnetization, tensor_spectrum
 from .fields import (anisotropy_field, dmi_field, exchange_field, linear_energy,
                      zeeman_energy, zeeman_field)
+from .layers import exchange_field_layers, layered_demag_fft, layered_tensor
 from .newell import demag_tensor
 
 
@@ -56,14 +57,24 @@ class Problem:
 
     Ms, A, Ku1, alpha: scalar or (nx, ny, nz); ku_axis: (3,) or (nx, ny, nz, 3);
     h_ext: (3,) in A/m or a callable t -> (3,); h_ext_weight: optional
-    (nx, ny, nz) multiplier of the external field; p: Newell radius."""
+    (nx, ny, nz) multiplier of the external field; p: Newell radius;
+    layers: optional nz layer thicknesses (Sec. 4.4, non-equidistant layers,
+    see ``oracle.layers``), which replace dx[2]; DMI is not defined there."""
 
     def __init__(self, n, dx, Ms, A, alpha, Ku1=0.0, ku_axis=(1.0, 0.0, 0.0),
                  h_ext=(0.0, 0.0, 0.0), h_ext_weight=None, p=20, demag=True, Nt=None, precession=True,
-                 D=0.0, dmi="interface"):
+                 D=0.0, dmi="interface", layers=None):
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
-        self.V = self.dx[0] * self.dx[1] * self.dx[2]
+        self.layers = None if layers is None else np.asarray(layers, dtype=np.float64)
+        if self.layers is not None:
+            if self.layers.shape != (self.n[2],) or np.any(self.layers <= 0):
+                raise ValueError("one positive thickness per layer")
+            if np.any(np.asarray(D) != 0):
+                raise ValueError("DMI with non-equidistant layers is not defined")
+            self.V = self.dx[0] * self.dx[1] * self.layers[None, None, :]
+        else:
+            self.V = self.dx[0] * self.dx[1] * self.dx[2]
         self.Ms = Ms
         self.A = A
         self.alpha = alpha
@@ -75,7 +86,9 @@ class Problem:
         self.precession = precession
         self.D = D
         self.dmi = dmi
-        if demag:
+        if demag and self.layers is not None:
+            self.Nt = layered_tensor(self.n, self.dx[0], self.dx[1], self.layers, p) if Nt is None else Nt
+        elif demag:
             self.Nt = demag_tensor(self.n, self.dx, p) if Nt is None else Nt
             self.Nhat = tensor_spectrum(self.Nt, self.n)
 
@@ -84,11 +97,16 @@ class Problem:
 
     def field_terms(self, m, t):
         terms = {}
-        if self.demag:
+        if self.demag and self.layers is not None:
+            terms["demag"] = layered_demag_fft(self.Nt, magnetization(m, self.Ms))
+        elif self.demag:
             terms["demag"] = demag_fft(self.Nt, magnetization(m, self.Ms), self.Nhat)
         else:
             terms["demag"] = np.zeros_like(m)
-        terms["exchange"] = exchange_field(m, self.Ms, self.A, self.dx)
+        if self.layers is not None:
+            terms["exchange"] = exchange_field_layers(m, self.Ms, self.A, self.dx[0], self.dx[1], self.layers)
+        else:
+            terms["exchange"] = exchange_field(m, self.Ms, self.A, self.dx)
         terms["anisotropy"] = anisotropy_field(m, self.Ms, self.Ku1, self.ku_axis)
         terms["zeeman"] = zeeman_field(self.h_ext_at(t), self.n, self.h_ext_weight)
         terms["dmi"] = dmi_field(m, self.Ms, self.D, self.dx, self.dmi)
