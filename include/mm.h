@@ -263,6 +263,25 @@ mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
  * MM_EINVAL for an unknown kind or a non-finite D. */
 mm_status mm_set_dmi(mm_state* s, mm_dmi_kind kind, double D, const double* D_cell, int on_device);
 
+/* Non-equidistant layers (Sec. 4.4): the grid's nz cells along z become
+ * layers of thickness h[0..nz-1] (metres, host array of nz doubles, copied),
+ * stacked without gaps from the bottom; the grid's dz is then unused.  Demag
+ * keeps the zero-padded FFT along x and y and couples the layers densely at
+ * every lateral wave number, with Newell's cell average for boxes of
+ * different thickness (the z stencil F(Z0) - F(Z0+h_i) - F(Z0-h_j) +
+ * F(Z0+h_i-h_j), divided by the target volume) within a Chebyshev distance p
+ * of (lateral offset, layer offset) and the source cell's point dipole
+ * beyond.  Exchange between layers k and k+1 is
+ * 2 A_link (m_{k+1} - m_k) / (mu0 Ms_k h_k (h_k + h_{k+1}) / 2) with the A of
+ * the two half cells in series, A_link = (h_k + h_{k+1}) A_k A_{k+1} /
+ * (h_k A_{k+1} + h_{k+1} A_k); energies use each cell's volume dx dy h_k.
+ * The demag tensor must be built again (mm_demag_setup) after this call; h =
+ * NULL returns to the equidistant grid.  Not with DMI (mm_set_dmi refuses
+ * either order), not in the adjoint, always through the unfused stage path.
+ * MM_EINVAL unless nz equals the grid's nz, 2 <= nz <= 64 and every h is
+ * finite and > 0. */
+mm_status mm_set_layers(mm_state* s, const double* h, int nz);
+
 /* Integrator options (Sec. 3): relax_method is the adaptive method mm_relax
  * uses (MM_DP45, the default, or MM_RKF45); precession = 0 drops the m x h
  * term of Eq. llg for every integrator of this state (the damping term keeps

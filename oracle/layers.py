@@ -218,3 +218,49 @@ def exchange_energy_links(m, A, dx, dy, h):
         Al = thickness_harmonic(A[:, :, k], A[:, :, k + 1], h[k], h[k + 1])
         E += float(np.sum(Al * dx * dy * np.sum((m[:, :, k + 1] - m[:, :, k]) ** 2, axis=-1) / d))
     return E
+
+
+def layered_demag_at(n, dx, dy, h, M, cells, p=20):
+    """Demag field at the listed target cells (x, y, layer) by the direct sum
+    over every source cell, the entries evaluated on the fly with the same
+    rule as layered_tensor: for spot checks of grids too large for the whole
+    tensor."""
+    nx, ny, nz = (int(v) for v in n)
+    h = np.asarray(h, dtype=np.float64)
+    z0 = layer_bottoms(h)
+    out = np.zeros((len(cells), 3))
+    for q, (x, y, i) in enumerate(cells):
+        I = (x - np.arange(nx))[:, None] + np.zeros((1, ny), dtype=int)
+        J = (y - np.arange(ny))[None, :] + np.zeros((nx, 1), dtype=int)
+        X, Y = I * float(dx), J * float(dy)
+        lat = np.maximum(np.abs(I), np.abs(J))
+        for j in range(nz):
+            near = np.ones(I.shape, dtype=bool) if p is None else (np.maximum(lat, abs(i - j)) <= p)
+            Z0 = z0[i] - z0[j]
+            N = np.zeros((6,) + I.shape)
+            for c, name in enumerate(COMP_NAMES):
+                if near.any():
+                    N[c][near] = layer_component(name, X[near], Y[near], Z0, float(dx), float(dy), h[i], h[j])
+                if (~near).any():
+                    N[c][~near] = layer_dipole(name, X[~near], Y[~near], Z0, float(dx), float(dy), h[i], h[j])
+            Mj = M[:, :, j]
+            out[q, 0] -= np.sum(N[0] * Mj[..., 0] + N[1] * Mj[..., 1] + N[2] * Mj[..., 2])
+            out[q, 1] -= np.sum(N[1] * Mj[..., 0] + N[3] * Mj[..., 1] + N[4] * Mj[..., 2])
+            out[q, 2] -= np.sum(N[2] * Mj[..., 0] + N[4] * Mj[..., 1] + N[5] * Mj[..., 2])
+    return out
+
+
+def layered_rounding_sensitivity(n, dx, dy, h, p, M, scales=(1e9, 3.7e8)):
+    """Floating-point noise of the oracle's own layered demag: the tensor is
+    dimensionless, so building it with lengths in other units must give the
+    same field; the largest relative max-norm change over the scales bounds
+    what an FP64 evaluation can reproduce (the 36-term stencil cancels
+    strongly at large offsets)."""
+    h = np.asarray(h, dtype=np.float64)
+    ref = layered_demag_fft(layered_tensor(n, dx, dy, h, p), M)
+    sc = np.max(np.abs(ref))
+    worst = 0.0
+    for s in scales:
+        hs = layered_demag_fft(layered_tensor(n, dx * s, dy * s, h * s, p), M)
+        worst = max(worst, float(np.max(np.abs(hs - ref)) / sc))
+    return worst

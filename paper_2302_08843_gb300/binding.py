@@ -27,7 +27,8 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
-           "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent")
+           "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent",
+           "mm_set_layers")
 
 
 class MMError(RuntimeError):
@@ -98,6 +99,7 @@ def lib():
         "mm_set_llg_options": (i, [vp, i, i]),
         "mm_set_dmi": (i, [vp, i, d, vp, i]),
         "mm_fft_extent": (i, [i]),
+        "mm_set_layers": (i, [vp, vp, i]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -296,6 +298,15 @@ class State:
             D_cell = np.ascontiguousarray(D_cell, dtype=np.float64)     # kept alive through the call
         p, dev = _ptr(D_cell)
         check(lib().mm_set_dmi(self.h, self.DMI_KINDS[kind], float(D), p, dev))
+
+    def set_layers(self, h=None):
+        """mm_set_layers: nz layer thicknesses in metres (None: equidistant
+        again); call demag_setup afterwards."""
+        if h is None:
+            check(lib().mm_set_layers(self.h, None, 0))
+            return
+        hh = np.ascontiguousarray(h, dtype=np.float64)
+        check(lib().mm_set_layers(self.h, hh.ctypes.data, int(hh.size)))
 
     def set_llg_options(self, relax_method="dp45", precession=True):
         """mm_set_llg_options: mm_relax's method ("dp45" or "rkf45") and the precession term."""

@@ -36,7 +36,15 @@ struct DemagDims {
     // 2-D grids: the z-pass kernels run along y (nz' = ny, Pz' = Py); the
     // odd components' mirror signs then come from the transformed axis
     int yz_swap = 0;
+    // non-equidistant layers (Sec. 4.4): no transform along z; the nz layers
+    // are coupled densely at every lateral wave number (p3_layers).  lh holds
+    // the nz thicknesses in the real type of the passes.
+    int layers = 0;
+    const void* lh = nullptr;
 };
+
+// most layers a non-equidistant stack may have (shared memory of p3_layers)
+constexpr int kMaxLayers = 64;
 
 // CUDA-event timing of kernel launches on a stream (inactive unless enabled).
 struct KernelTimer {
@@ -114,6 +122,11 @@ struct StageParams {
     T dmi_e[9];                  // DMI vectors e_x, e_y, e_z (each 3 components)
     T i2dx, i2dy, i2dz;          // 1 / (2 d) per axis
     int no_precession;           // drop the m x h summand of the LLG right-hand side
+    // non-equidistant layers: lay[k] = h_k, lay[nz + k] = 2 / (h_k (h_k + h_{k+1})),
+    // lay[2 nz + k] = 2 / (h_k (h_{k-1} + h_k)) (0 at the stack's ends), lvol[k] =
+    // dx dy h_k; null: equidistant (idz2 and V)
+    const T* lay;
+    const double* lvol;
     double* partials;            // [number of blocks][kNPart]
     // the coefficients above in the field type (filled by launch_stage)
     T kcT[7], ckT, dtT, acc_bT;

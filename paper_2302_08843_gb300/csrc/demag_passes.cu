@@ -863,6 +863,69 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
     }
 }
 
+// ----------------------------------------------------------- P3 layers ----
+// Non-equidistant layers (Sec. 4.4): no transform along z; at every lateral
+// wave number (kx, ky) the nz layers are coupled densely,
+//   h^_i = sum_j K_ij(kx, ky) M^_j,
+// with K_ij the 2-D spectrum of the layer-pair tensor (scaled by -1/(Px Py)).
+// Only pairs i <= j are stored; K_ij for i > j is (h_j / h_i) K_ji(-k), which
+// keeps the real components and flips the sign of the -i t ones (xz, yz).
+// A CTA takes 32 kx columns of one ky (the mirrored ky = Py - p next to it, so
+// both read the tensor row p while it is in L2), parks the 3 nz inputs of its
+// columns in shared memory, then each thread row computes whole layers and
+// writes them back in place.
+constexpr int kLayCols = 32, kLayRows = 8;
+
+__host__ __device__ constexpr int layer_pair(int i, int j, int nz) { return i * nz - i * (i - 1) / 2 + (j - i); }
+
+template <typename T>
+__global__ void __launch_bounds__(kLayCols * kLayRows)
+p3_layers(DemagDims d, typename Cplx<T>::type* __restrict__ S, const T* __restrict__ tens) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);      // [3 nz][kLayCols]
+    const int nz = d.nz, LY = d.LY, KY2 = LY / 2 + 1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int kx = blockIdx.x * kLayCols + tx;
+    const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
+    const bool row_ok = p < KY2 && (side == 0 || (p > 0 && 2 * p < LY));
+    const bool valid = row_ok && kx < d.KX;
+    const int ky = side ? LY - p : p;
+    const long zs = (long)LY * d.KXS;                       // one (component, layer) plane
+    C* col = S + (long)blockIdx.z * 3 * nz * zs + (long)ky * d.KXS + kx;
+    for (int q = ty; q < 3 * nz; q += kLayRows) sm[q * kLayCols + tx] = valid ? col[q * zs] : mk<C>(0, 0);
+    __syncthreads();
+    if (!valid) return;
+    const T sy = side ? (T)-1 : (T)1;                       // odd in y: xy, yz
+    const long prow = (long)KY2 * d.KXS;                    // one pair
+    const long tc = (long)(nz * (nz + 1) / 2) * prow;       // one component
+    const T* t0 = tens + (long)p * d.KXS + kx;
+    const T* lh = static_cast<const T*>(d.lh);
+    for (int i = ty; i < nz; i += kLayRows) {
+        const T hi = lh[i];
+        T hxr = 0, hxi = 0, hyr = 0, hyi = 0, hzr = 0, hzi = 0;
+        for (int j = 0; j < nz; ++j) {
+            const bool lo = i <= j;
+            const T* tp = t0 + (long)(lo ? layer_pair(i, j, nz) : layer_pair(j, i, nz)) * prow;
+            const T r = lo ? (T)1 : lh[j] / hi;
+            const T so = lo ? r : -r;                          // K(-k) flips the single-odd components
+            const T txx = r * __ldg(tp), txy = r * sy * __ldg(tp + tc), txz = so * __ldg(tp + 2 * tc);
+            const T tyy = r * __ldg(tp + 3 * tc), tyz = so * sy * __ldg(tp + 4 * tc), tzz = r * __ldg(tp + 5 * tc);
+            const C mx = sm[j * kLayCols + tx], my = sm[(nz + j) * kLayCols + tx], mz = sm[(2 * nz + j) * kLayCols + tx];
+            // xz and yz are -i t: (-i t)(a + i b) = t b - i t a
+            hxr += txx * mx.x + txy * my.x + txz * mz.y;
+            hxi += txx * mx.y + txy * my.y - txz * mz.x;
+            hyr += txy * mx.x + tyy * my.x + tyz * mz.y;
+            hyi += txy * mx.y + tyy * my.y - tyz * mz.x;
+            hzr += txz * mx.y + tyz * my.y + tzz * mz.x;
+            hzi += -txz * mx.x - tyz * my.x + tzz * mz.y;
+        }
+        col[(long)i * zs] = mk<C>(hxr, hxi);
+        col[(long)(nz + i) * zs] = mk<C>(hyr, hyi);
+        col[(long)(2 * nz + i) * zs] = mk<C>(hzr, hzi);
+    }
+}
+
 // Persistent TMA variant of the register-resident z pass (FP32, Pz <= 256):
 // tile = (16 kx columns, one ky); tiles run ky = 0, 1, Py-1, 2, Py-2, ... so
 // that the two wave numbers sharing a tensor slice are neighbours in time.
@@ -1420,9 +1483,36 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
 // P2 .. P4: S1 -> S1 through the tensor multiply.  A 2-D grid (nz = 1, Py <= 256)
 // runs the z-pass kernel along y in place on S1 instead (one pass, no S2).
 template <typename T>
+static void launch_p3_layers(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    const size_t sm = (size_t)3 * d.nz * kLayCols * sizeof(C);
+    auto k = p3_layers<T>;
+    set_smem(k, sm);
+    dim3 grid((d.KX + kLayCols - 1) / kLayCols, 2 * (d.LY / 2 + 1), d.nb);
+    k<<<grid, dim3(kLayCols, kLayRows), sm, st>>>(d, S2, tens);
+}
+
+template <typename T>
 static void yzy(const DemagDims& d, typename Cplx<T>::type* S1, typename Cplx<T>::type* S2, const T* tens,
                 cudaStream_t st, KernelTimer* tm) {
     using C = typename Cplx<T>::type;
+    if (d.layers) {
+        C* S2l = d.LY == 1 ? S1 : S2;
+        if (d.LY > 1) {
+            tm->begin(st, "p2_y_forward");
+            MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
+            tm->end(st);
+        }
+        tm->begin(st, "p3_layers");
+        launch_p3_layers<T>(d, S2l, tens, st);
+        tm->end(st);
+        if (d.LY > 1) {
+            tm->begin(st, "p4_y_inverse");
+            MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
+            tm->end(st);
+        }
+        return;
+    }
     if (d.nz == 1 && d.LY > 1 && d.LY <= 256) {
         DemagDims d2 = d;
         d2.ny = 1; d2.nz = d.ny; d2.LY = 1; d2.LZ = d.LY; d2.yz_swap = 1;
@@ -1480,6 +1570,7 @@ bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cu
 }
 
 bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
+    if (d.layers || p.lay) return false;
     if (!d.err || d.LX < 16 || d.LX > 4096 || !is_pow2(d.LX) || d.nx % 2 != 0) return false;
     if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f) return false;
     const int threads = (3 * kK5Rows / 2) * (d.LX / 16);

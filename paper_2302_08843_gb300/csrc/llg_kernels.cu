@@ -39,6 +39,14 @@ __device__ __forceinline__ T harmonic(T a, T b) {
     return s != (T)0 ? (T)2 * a * b / s : (T)0;
 }
 
+// A of a link between cells of thickness ha, hb in series (non-equidistant
+// layers): (ha + hb) a b / (ha b + hb a), the harmonic mean when ha = hb
+template <typename T>
+__device__ __forceinline__ T thick_harmonic(T a, T b, T ha, T hb) {
+    const T s = ha * b + hb * a;
+    return s != (T)0 ? (ha + hb) * a * b / s : (T)0;
+}
+
 // VEC consecutive cells along x per thread (float4 / double2 loads).
 template <typename T, int VEC> struct Vec;
 template <> struct Vec<float, 4> {
@@ -151,8 +159,27 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
         }
         MM_VLINK(y > 0, -sy, p.idy2)
         MM_VLINK(y < ny - 1, sy, p.idy2)
-        MM_VLINK(z > 0, -sz, p.idz2)
-        MM_VLINK(z < nz - 1, sz, p.idz2)
+        if (!p.lay) {
+            MM_VLINK(z > 0, -sz, p.idz2)
+            MM_VLINK(z < nz - 1, sz, p.idz2)
+        } else {
+            // non-equidistant layers: 2 A_link / (h_k (h_k + h_nb)) per z link, A_link in series
+            const T hk = p.lay[z];
+#define MM_LLINK(COND, OFF, COEF, HNB)                                                    \
+            if (COND) {                                                                   \
+                const T c = (COEF), hn = (HNB);                                           \
+                T nbx[VEC], nby[VEC], nbz[VEC], Anb[VEC];                                 \
+                LV::ld(m + i + (OFF), nbx); LV::ld(m + N + i + (OFF), nby); LV::ld(m + 2 * N + i + (OFF), nbz); \
+                if (a_cell) LV::ld(p.A_cell + i + (OFF), Anb);                            \
+                _Pragma("unroll") for (int v = 0; v < VEC; ++v) {                          \
+                    const T w = (a_cell ? thick_harmonic(A[v], Anb[v], hk, hn) : p.A) * c; \
+                    sx[v] += w * (nbx[v] - mx[v]); sy_[v] += w * (nby[v] - my[v]); sz_[v] += w * (nbz[v] - mz[v]); \
+                }                                                                         \
+            }
+            MM_LLINK(z > 0, -sz, p.lay[2 * nz + z], p.lay[z > 0 ? z - 1 : z])
+            MM_LLINK(z < nz - 1, sz, p.lay[nz + z], p.lay[z < nz - 1 ? z + 1 : z])
+#undef MM_LLINK
+        }
 #undef MM_VLINK
         // DMI (Sec. 4.3): dm_i = sum_axes e_a x (Dt_+ m_{i+a} - Dt_- m_{i-a}) / (2 d_a); a neighbour
         // outside the grid is left out; Dt the link average of D (D itself when uniform)
@@ -244,7 +271,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> 
             if (p.want_torque && Ms[v] != (T)0)
                 red_torque = fmax(red_torque, sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms[v]);
             if (p.want_energy && Ms[v] != (T)0) {
-                const double f = -0.5 * kMu0 * p.V * (double)Ms[v];
+                const double f = -0.5 * kMu0 * (p.lvol ? p.lvol[z] : p.V) * (double)Ms[v];
                 red_e0 += f * ((double)mx[v] * hdxv + (double)my[v] * hdyv + (double)mz[v] * hdzv);
                 red_e1 += f * ((double)mx[v] * hex + (double)my[v] * hey + (double)mz[v] * hez);
                 red_e2 += f * ((double)mx[v] * hax + (double)my[v] * hay + (double)mz[v] * haz);

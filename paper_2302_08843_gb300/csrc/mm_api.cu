@@ -187,6 +187,11 @@ struct mm_state {
     mm_method relax_method = MM_DP45;
     bool s1_fresh = false;   // S1 holds the x-spectrum of Ms m for the current m (left by the fused RK4 path)
     bool use_fused = true;   // RK4 in FP32 may take the fused stage kernel
+    // non-equidistant layers: thicknesses (host), per-layer coefficients
+    // (3 nz of the real type, StageParams::lay) and cell volumes (nz doubles)
+    std::vector<double> lay_h;
+    void* lay_t = nullptr;
+    double* lay_v = nullptr;
     KernelTimer timer;
 };
 
@@ -284,6 +289,10 @@ template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, con
     p.mn = (const T*)s->m;
     p.no_precession = s->precession ? 0 : 1;
     p.i2dx = (T)(0.5 / s->g.dx); p.i2dy = (T)(0.5 / s->g.dy); p.i2dz = (T)(0.5 / s->g.dz);
+    if (!s->lay_h.empty()) {
+        p.lay = (const T*)s->lay_t;
+        p.lvol = s->lay_v;
+    }
     if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell)) {
         // DMI vectors e_x, e_y, e_z of the paper's table (e_{-k} = -e_k)
         static const double vecs[4][9] = {{0, 0, 0, 0, 0, 0, 0, 0, 0},
@@ -1007,7 +1016,7 @@ void mm_state_destroy(mm_state* s) {
     void** bufs[] = {&s->m, &s->mA, &s->mB, &s->acc, &s->hd, &s->S1, &s->S2, &s->tens, &s->D_cell, &s->Ms_cell,
                      &s->A_cell, &s->Ku_cell, &s->alpha_cell, &s->axis_tab, reinterpret_cast<void**>(&s->grain),
                      &s->zw, reinterpret_cast<void**>(&s->partials), reinterpret_cast<void**>(&s->scalars),
-                     reinterpret_cast<void**>(&s->dev_err)};
+                     reinterpret_cast<void**>(&s->dev_err), &s->lay_t, reinterpret_cast<void**>(&s->lay_v)};
     for (void** b : bufs) dev_free(*b);
     for (int q = 0; q < 7; ++q) dev_free(s->K[q]);
     for (int q = 0; q < 19; ++q) dev_free(s->adj[q]);
@@ -1086,7 +1095,10 @@ mm_status mm_demag_setup(mm_state* s, int p_newell) {
     const double dd[3] = {s->g.dx, s->g.dy, s->g.dz};
     const int P[3] = {s->d.LX, s->d.LY, s->d.LZ};
     std::vector<double> spec;
-    tensor_spectrum(n, dd, p_newell, P, s->d.KXS, spec);
+    if (!s->lay_h.empty())
+        tensor_layers_spectrum(n[0], n[1], n[2], dd[0], dd[1], s->lay_h.data(), p_newell, P[0], P[1], s->d.KXS, spec);
+    else
+        tensor_spectrum(n, dd, p_newell, P, s->d.KXS, spec);
     const long cnt = (long)spec.size();
     dev_free(s->tens);
     MM_TRY(dev_alloc(&s->tens, s->rsz * (size_t)cnt));
@@ -1191,6 +1203,7 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
     if (lambda_n == lambda_np1 || lambda_n == m_n) return fail(MM_EINVAL, "lambda_n must not alias the inputs");
     if (!s->precession) return fail(MM_EINVAL, "the adjoint is written for the LLG right-hand side with precession");
+    if (!s->lay_h.empty()) return fail(MM_EINVAL, "the adjoint does not cover non-equidistant layers");
     if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell))
         return fail(MM_EINVAL, "the adjoint does not cover the DMI term");
     MM_TRY(ready_for_fields(s));
@@ -1203,6 +1216,8 @@ mm_status mm_set_dmi(mm_state* s, mm_dmi_kind kind, double D, const double* D_ce
     MM_TRY(check_state(s));
     if (kind < MM_DMI_NONE || kind > MM_DMI_D2D) return fail(MM_EINVAL, "unknown DMI kind %d", (int)kind);
     if (!std::isfinite(D)) return fail(MM_EINVAL, "D must be finite");
+    if (kind != MM_DMI_NONE && !s->lay_h.empty())
+        return fail(MM_EINVAL, "DMI is not defined with non-equidistant layers");
     MM_TRY(set_device(s));
     MM_TRY(upload_real(s, kind == MM_DMI_NONE ? nullptr : D_cell, s->N, on_device, &s->D_cell));
     s->dmi_kind = kind;
@@ -1228,6 +1243,52 @@ mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins) {
     if (spins < 1) return fail(MM_EINVAL, "spins must be >= 1");
     launch_diag_wait(s->dev_err, spins, s->st);
     MM_LAUNCHED();
+    return MM_OK;
+}
+
+mm_status mm_set_layers(mm_state* s, const double* h, int nz) {
+    MM_TRY(check_state(s));
+    if (!h) {
+        if (s->lay_h.empty()) return MM_OK;
+    } else {
+        if (nz != s->g.nz) return fail(MM_EINVAL, "need one thickness per layer (%d), got %d", s->g.nz, nz);
+        if (nz < 2 || nz > kMaxLayers) return fail(MM_EINVAL, "a layer stack has 2 to %d layers", kMaxLayers);
+        for (int k = 0; k < nz; ++k)
+            if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(MM_EINVAL, "layer %d thickness must be > 0", k);
+        if (s->dmi_kind != MM_DMI_NONE) return fail(MM_EINVAL, "DMI is not defined with non-equidistant layers");
+    }
+    MM_TRY(set_device(s));
+    MM_CUDA(cudaStreamSynchronize(s->st));
+    dev_free(s->lay_t);
+    dev_free(reinterpret_cast<void*&>(s->lay_v));
+    s->lay_t = nullptr;
+    s->lay_v = nullptr;
+    s->lay_h.clear();
+    s->d.layers = 0;
+    s->d.lh = nullptr;
+    // the tensor of the old geometry no longer applies
+    s->demag_ready = false;
+    s->fsal = s->k1_exact = s->s1_fresh = false;
+    if (!h) return MM_OK;
+    std::vector<double> t(3 * (size_t)nz, 0.0), v(nz);
+    for (int k = 0; k < nz; ++k) {
+        t[k] = h[k];
+        if (k < nz - 1) t[nz + k] = 2.0 / (h[k] * (h[k] + h[k + 1]));
+        if (k > 0) t[2 * nz + k] = 2.0 / (h[k] * (h[k - 1] + h[k]));
+        v[k] = s->g.dx * s->g.dy * h[k];
+    }
+    MM_TRY(dev_alloc(&s->lay_t, s->rsz * t.size()));
+    MM_TRY(dev_alloc(reinterpret_cast<void**>(&s->lay_v), sizeof(double) * nz));
+    if (s->prec == MM_FP64) {
+        MM_CUDA(cudaMemcpy(s->lay_t, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(t.begin(), t.end());
+        MM_CUDA(cudaMemcpy(s->lay_t, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+    }
+    MM_CUDA(cudaMemcpy(s->lay_v, v.data(), sizeof(double) * nz, cudaMemcpyHostToDevice));
+    s->lay_h.assign(h, h + nz);
+    s->d.layers = 1;
+    s->d.lh = s->lay_t;
     return MM_OK;
 }
 

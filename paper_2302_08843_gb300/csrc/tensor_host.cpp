@@ -250,6 +250,110 @@ void tensor_spectrum(const int n[3], const double d[3], int p, const int P[3], i
     }
 }
 
+// ------------------------------------------------ non-equidistant layers ----
+// Cell average between boxes of different thickness: along z, where equal
+// cells combine 2 F(Z) - F(Z + c) - F(Z - c), a target box of thickness hi and
+// a source box of thickness hj whose lower faces are Z0 apart combine
+// F(Z0) - F(Z0 + hi) - F(Z0 - hj) + F(Z0 + hi - hj); the sum is divided by the
+// target volume.  z is the third argument of f / g for xx, yy, xy, the first
+// for zz and the second for xz, yz (the same permutations as newell_comp).
+static double layer_comp(int comp, double X, double Y, double Z0, double a, double b, double hi, double hj) {
+    const double zs[4] = {Z0, Z0 + hi, Z0 - hj, Z0 + hi - hj};
+    const double wz[4] = {1.0, -1.0, -1.0, 1.0};
+    double acc = 0.0;
+    for (int i = -1; i <= 1; ++i) {
+        const double wi = i == 0 ? 2.0 : -1.0;
+        const double x = X + i * a;
+        for (int j = -1; j <= 1; ++j) {
+            const double wj = j == 0 ? 2.0 : -1.0;
+            const double y = Y + j * b;
+            for (int k = 0; k < 4; ++k) {
+                const double z = zs[k];
+                double v;
+                switch (comp) {
+                    case 0: v = newell_f(x, y, z); break;
+                    case 3: v = newell_f(y, x, z); break;
+                    case 5: v = newell_f(z, y, x); break;
+                    case 1: v = newell_g(x, y, z); break;
+                    case 2: v = newell_g(x, z, y); break;
+                    default: v = newell_g(y, z, x); break;
+                }
+                acc += wi * wj * wz[k] * v;
+            }
+        }
+    }
+    return acc / (4.0 * M_PI * a * b * hi);
+}
+
+// lateral parity of each component (x, y): true = odd
+static const bool kOddL[6][2] = {{false, false}, {true, true}, {true, false},
+                                 {false, false}, {false, true}, {false, false}};
+
+void tensor_layers_spectrum(int nx, int ny, int nz, double dx, double dy, const double* h, int p, int Px, int Py,
+                            int kx_stride, std::vector<double>& spec) {
+    const int KX = Px / 2 + 1, KY = Py / 2 + 1;
+    const int npair = nz * (nz + 1) / 2;
+    std::vector<double> z0(nz, 0.0);
+    for (int k = 1; k < nz; ++k) z0[k] = z0[k - 1] + h[k - 1];
+    // real-space entries at X, Y >= 0 for every stored pair: oct[c][q][Y][X]
+    const size_t cnt = (size_t)nx * ny;
+    std::vector<double> oct((size_t)6 * npair * cnt, 0.0);
+    std::vector<int> qi(npair), qj(npair);
+    for (int i = 0, q = 0; i < nz; ++i)
+        for (int j = i; j < nz; ++j, ++q) { qi[q] = i; qj[q] = j; }
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int q = 0; q < npair; ++q)
+        for (int Y = 0; Y < ny; ++Y)
+            for (int X = 0; X < nx; ++X) {
+                const int i = qi[q], j = qj[q];
+                const int lat = X > Y ? X : Y;
+                const int cheb = lat > (j - i) ? lat : (j - i);
+                const bool near = p < 0 || cheb <= p;
+                const double Xm = X * dx, Ym = Y * dy, Z0 = z0[i] - z0[j];
+                const double Zc = Z0 + 0.5 * (h[i] - h[j]);       // centre offset for the dipole
+                for (int c = 0; c < 6; ++c)
+                    oct[((size_t)c * npair + q) * cnt + (size_t)Y * nx + X] =
+                        near ? layer_comp(c, Xm, Ym, Z0, dx, dy, h[i], h[j])
+                             : dipole_comp(c, Xm, Ym, Zc, dx * dy * h[j]);
+            }
+    const size_t out_cnt = (size_t)KY * kx_stride;
+    spec.assign((size_t)6 * npair * out_cnt, 0.0);
+    const double scale = -1.0 / ((double)Px * (double)Py);
+    std::vector<double> tx[2], ty[2];
+    for (int o = 0; o < 2; ++o) {
+        axis_table(nx, Px, KX, o == 1, tx[o]);
+        axis_table(ny, Py, KY, o == 1, ty[o]);
+    }
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int c = 0; c < 6; ++c)
+        for (int q = 0; q < npair; ++q) {
+            const double* f = oct.data() + ((size_t)c * npair + q) * cnt;
+            const std::vector<double>& Tx = tx[kOddL[c][0]];
+            const std::vector<double>& Ty = ty[kOddL[c][1]];
+            std::vector<double> a((size_t)ny * KX);
+            for (int Y = 0; Y < ny; ++Y)
+                for (int kx = 0; kx < KX; ++kx) {
+                    const double* t = Tx.data() + (size_t)kx * nx;
+                    double acc = 0.0;
+                    for (int X = 0; X < nx; ++X) acc += t[X] * f[(size_t)Y * nx + X];
+                    a[(size_t)Y * KX + kx] = acc;
+                }
+            // two odd axes: (-i)^2 = -1; one odd axis: the -i stays with the kernel
+            const double sg = (kOddL[c][0] && kOddL[c][1] ? -1.0 : 1.0) * scale;
+            double* outc = spec.data() + ((size_t)c * npair + q) * out_cnt;
+            for (int ky = 0; ky < KY; ++ky) {
+                double* orow = outc + (size_t)ky * kx_stride;
+                for (int Y = 0; Y < ny; ++Y) {
+                    const double w = Ty[(size_t)ky * ny + Y];
+                    if (w == 0.0) continue;
+                    const double* ar = a.data() + (size_t)Y * KX;
+                    for (int kx = 0; kx < KX; ++kx) orow[kx] += w * ar[kx];
+                }
+                for (int kx = 0; kx < KX; ++kx) orow[kx] *= sg;
+            }
+        }
+}
+
 void twiddle_entry(int L, int m, double* re, double* im) {
     double c, s;
     unit_root(L, m, &c, &s);

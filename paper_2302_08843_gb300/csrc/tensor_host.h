@@ -19,6 +19,19 @@ void tensor_full_offsets(const int n[3], const double d[3], int p, double* out);
 void tensor_spectrum(const int n[3], const double d[3], int p, const int P[3], int kx_stride,
                      std::vector<double>& spec);
 
+// Non-equidistant layers (Sec. 4.4): tensor between a target cell of layer i
+// and a source cell of layer j (thicknesses h[i], h[j], stacked without gaps)
+// at lateral offset (X dx, Y dy), transformed over the two lateral axes of the
+// padded grid Px x Py.  Only pairs i <= j are stored (the rest follow from
+// h_i N_ij(r) = h_j N_ji(-r)); pair index q(i, j) = i nz - i (i - 1) / 2 + j - i.
+// Layout spec[c][q][ky][kx], ky <= Py/2, kx <= Px/2, row stride kx_stride,
+// scaled by -1/(Px Py).  xx, xy, yy, zz are the real spectra; for xz and yz
+// (odd along one lateral axis) the stored t gives the spectrum -i t.  Newell
+// where max(|X|, |Y|, |i - j|) <= p (p < 0: always), the point dipole of the
+// source cell beyond.
+void tensor_layers_spectrum(int nx, int ny, int nz, double dx, double dy, const double* h, int p, int Px, int Py,
+                            int kx_stride, std::vector<double>& spec);
+
 // exp(-2 pi i m / L), m in [0, L), with exact octant symmetry.
 void twiddle_table(int L, std::vector<double>& re, std::vector<double>& im);
 void twiddle_entry(int L, int m, double* re, double* im);

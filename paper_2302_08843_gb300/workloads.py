@@ -22,6 +22,12 @@ Workloads (sizes and materials as used for the benchmark and parity tests):
 * ``inverse_design``: 128x128x1 cells of 5 nm, Ms = sigmoid(w) 8e5 with
                     w ~ N(0, 0.1) (seed 5), A 1.3e-11, alpha 0.05, 5 mT sinc
                     excitation along y in the strip x < 10 cells, m0 = +x.
+* ``multilayer``  : 256x256x8 cells of 2x2 nm laterally in 8 layers of
+                    unequal thickness (1.0, 0.6, 2.4, 0.8, 1.5, 0.6, 3.0, 1.1 nm,
+                    repeated / cut for other nz), alternating materials per
+                    layer: thick layers Ms 1.1e6, A 1.6e-11, Ku1 3e5 along z;
+                    0.6 nm layers Ms 4e5, A 0.4e-11; the rest Ms 8e5, A 1.3e-11;
+                    alpha 0.1, 20 mT along x, random unit m0 (seed 6), RK4 dt 2e-14 s.
 * ``serving_stream``: 512 relax requests, Poisson arrivals (mean 2 ms, seed 4),
                     grids from {64x64x1, 128x32x4, 100x100x8, 200x50x2, 256x256x1},
                     3 nm cubes, Ms ~ U[6e5, 1.2e6], A ~ U[1e-11, 2e-11], alpha 1.
@@ -171,6 +177,32 @@ def inverse_design(seed=5, n=(128, 128, 1), strip=10, out_box=((108, 118), (59, 
 
 
 SERVING_GRIDS = ((64, 64, 1), (128, 32, 4), (100, 100, 8), (200, 50, 2), (256, 256, 1))
+
+
+MULTILAYER_THICKNESS_NM = (1.0, 0.6, 2.4, 0.8, 1.5, 0.6, 3.0, 1.1)
+
+
+def multilayer(seed=6, n=(256, 256, 8)):
+    """Non-equidistant stack; the thicknesses are in ``extra["layers"]``."""
+    n = tuple(int(v) for v in n)
+    nz = n[2]
+    h = np.array([MULTILAYER_THICKNESS_NM[k % len(MULTILAYER_THICKNESS_NM)] for k in range(nz)]) * 1e-9
+    Ms_l, A_l, Ku_l = np.empty(nz), np.empty(nz), np.empty(nz)
+    for k in range(nz):
+        if h[k] >= 1.5e-9:
+            Ms_l[k], A_l[k], Ku_l[k] = 1.1e6, 1.6e-11, 3e5
+        elif h[k] <= 0.6e-9:
+            Ms_l[k], A_l[k], Ku_l[k] = 4e5, 0.4e-11, 0.0
+        else:
+            Ms_l[k], A_l[k], Ku_l[k] = 8e5, 1.3e-11, 0.0
+    shape = n
+    rng = np.random.default_rng(seed)
+    m0 = _unit(rng.normal(size=n + (3,)))
+    return Workload("multilayer %dx%dx%d" % n, n, (2e-9, 2e-9, float(h.mean())),
+                    Ms=np.broadcast_to(Ms_l, shape).copy(), A=np.broadcast_to(A_l, shape).copy(),
+                    alpha=0.1, m0=m0, Ku1=np.broadcast_to(Ku_l, shape).copy(), ku_axis=(0.0, 0.0, 1.0),
+                    h_ext=(0.020 / MU0_FOR_INPUTS, 0.0, 0.0), dt=2e-14, steps=1, method="rk4",
+                    extra={"layers": h})
 
 
 def serving_stream(seed=4, count=512, mean_gap=2e-3):
