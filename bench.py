@@ -408,12 +408,82 @@ def b1_cufft_measure(torch, w, steps, warmup, s32):
                     "PyTorch kernels, FP32"}
 
 
-def workloads_measure(torch):
+def layers_bytes(n, s):
+    """Algorithmic HBM bytes of one p3_layers launch for real size s: the 3 nz
+    complex planes of the y-spectrum read and written once, and the tensor's
+    stored pairs i <= j read once (the mirrored ky reads the same row)."""
+    nx, ny, nz = n
+    LX, LY, _ = padded(n)
+    KX = LX // 2 + 1
+    spectrum = 2 * 3 * nz * KX * LY * 2 * s
+    tensor = 6 * (nz * (nz + 1) // 2) * (LY // 2 + 1) * KX * s
+    return spectrum + tensor
+
+
+def layers_measure(torch, hbm_peak, steps=20, warmup=3):
+    """The non-equidistant stack (Sec. 4.4): 256x256x8 cells in 8 layers of
+    unequal thickness, per-layer materials, RK4 in FP32 and FP64 fields;
+    cell-updates/s per RK stage (device-timed, no per-kernel events), then a
+    profiled run of the same steps for the per-kernel split and the coupling
+    pass against the HBM roofline."""
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import State
+    from paper_2302_08843_gb300.workloads import to_soa
+    w = W.multilayer()
+    out = {"layers_nm": [round(v * 1e9, 3) for v in w.extra["layers"]]}
+    stream = torch.cuda.current_stream()
+    for prec, rs in (("fp32", 4), ("fp64", 8)):
+        s = State(w.n, w.dx, prec, stream)
+        s.set_material(Ms=0.0, A=0.0, alpha=w.alpha, Ku1=0.0, ku_axis=w.ku_axis,
+                       Ms_cell=to_soa(w.Ms), A_cell=to_soa(w.A), Ku1_cell=to_soa(w.Ku1))
+        s.set_zeeman(h=w.h_ext)
+        s.set_layers(w.extra["layers"])
+        s.demag_setup(20)
+        s.set_m(to_soa(w.m0))
+        t = 0.0
+        for _ in range(warmup):
+            t, _ = s.step(w.dt, t, "rk4")
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            t, _ = s.step(w.dt, t, "rk4")
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        s.profile_enable(True)
+        for _ in range(steps):
+            t, _ = s.step(w.dt, t, "rk4")
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile_enable(False)
+        s.close()
+        tot = sum(v[1] for v in prof.values())
+        split = {k: {"launches": v[0], "us_per_launch": round(1e3 * v[1] / max(v[0], 1), 2),
+                     "share": round(v[1] / tot, 4)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        ent = {"ms_per_step": round(ms / steps, 4),
+               "cell_updates_per_s": w.ncells * 4 * steps / (ms / 1e3),
+               "kernels": split}
+        if "p3_layers" in prof:
+            n_l, t_l = prof["p3_layers"]
+            us = 1e3 * t_l / n_l
+            byt = layers_bytes(w.n, rs)
+            ent["p3_layers_roofline"] = {"algorithmic_bytes": byt, "us": round(us, 2),
+                                         "achieved_gbs": round(byt / (us * 1e-6) / 1e9, 1),
+                                         "frac_of_measured_hbm": round(byt / (us * 1e-6) / 1e9 / hbm_peak, 4)}
+        out[prec] = ent
+    torch.cuda.empty_cache()
+    return out
+
+
+def workloads_measure(torch, hbm_peak=6800.0):
     """Time to solution of the paper-shaped configurations beside the bulk one
     (wall time with the device synchronised): plain FP64 (32x32x4, 200 RK4
     steps), the thin film (512x128x1, DP45 with rtol 1e-5 to 1 ns, FP64 and
-    FP32 fields) and the inverse design (128x128x1, 2000 FP32 RK4 steps and the
-    gradient of the time-averaged output m_y by the checkpointed adjoint)."""
+    FP32 fields), the inverse design (128x128x1, 2000 FP32 RK4 steps and the
+    gradient of the time-averaged output m_y by the checkpointed adjoint) and
+    the non-equidistant multilayer (256x256x8, RK4, layers_measure)."""
     from paper_2302_08843_gb300 import workloads as W
     from paper_2302_08843_gb300.autodiff import rk4_observable
     from paper_2302_08843_gb300.binding import State, setup_workload
@@ -471,6 +541,7 @@ def workloads_measure(torch):
                                                        "checkpoint_every": 100}
     s.close()
     torch.cuda.empty_cache()
+    out["multilayer_256x256x8_rk4"] = layers_measure(torch, hbm_peak)
     return out
 
 
@@ -601,7 +672,7 @@ def run_ours(args):
     serving = None
     if args.serve_requests > 0 and not args.nz:
         serving = serve_measure(torch, args.serve_requests, dist, rank, ws)
-    other = workloads_measure(torch) if (rank == 0 and not args.nz and not args.no_workloads) else None
+    other = workloads_measure(torch, hbm_peak) if (rank == 0 and not args.nz and not args.no_workloads) else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -733,6 +804,14 @@ def run_reference(args):
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_layers_only(args):
+    import torch
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    res = layers_measure(torch, peaks.get("hbm_gbs", 6800.0), steps=args.steps, warmup=args.warmup)
+    print(json.dumps({"case": "multilayer 256x256x8 (profiling case)", "layers": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -747,10 +826,15 @@ def main():
                          "result)")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the served stream to run (512 = all; 0 = skip)")
+    ap.add_argument("--layers-only", action="store_true",
+                    help="profiling case: only the 256x256x8 non-equidistant stack (the printed line is not a "
+                         "bench result)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.layers_only:
+        run_layers_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

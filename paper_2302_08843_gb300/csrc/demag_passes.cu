@@ -868,23 +868,53 @@ p3_z_conv_reg(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __r
 // wave number (kx, ky) the nz layers are coupled densely,
 //   h^_i = sum_j K_ij(kx, ky) M^_j,
 // with K_ij the 2-D spectrum of the layer-pair tensor (scaled by -1/(Px Py)).
-// Only pairs i <= j are stored; K_ij for i > j is (h_j / h_i) K_ji(-k), which
-// keeps the real components and flips the sign of the -i t ones (xz, yz).
+// Only pairs i <= j are stored, for ky <= Py/2.  Two sign identities fold
+// the rest into the operands:
+//   * the mirrored row ky = Py - p flips the components odd in y (xy, yz):
+//     K(Py - p) = E K(p) E with E = diag(1, -1, 1);
+//   * h_i N_ij(r) = h_j N_ji(-r) gives K_ij(k) = (h_j / h_i) K_ji(-k), and -k
+//     flips the single-odd components (xz, yz): K(-k) = D K(k) D with
+//     D = diag(1, 1, -1).
+// So with P_j = E M^_j and Q_j = h_j D P_j (both parked in shared memory),
+//   h^_i = E [ sum_{j >= i} K_ij P_j + (1 / h_i) D sum_{j < i} K_ji Q_j ],
+// and the inner loops are plain multiply-adds of stored entries.
 // A CTA takes 32 kx columns of one ky (the mirrored ky = Py - p next to it, so
-// both read the tensor row p while it is in L2), parks the 3 nz inputs of its
-// columns in shared memory, then each thread row computes whole layers and
-// writes them back in place.
+// both read the tensor row p while it is in L2); each thread row computes
+// whole layers and writes them back in place once every input is parked.
 constexpr int kLayCols = 32, kLayRows = 8;
 
 __host__ __device__ constexpr int layer_pair(int i, int j, int nz) { return i * nz - i * (i - 1) / 2 + (j - i); }
+
+// acc += K v for one stored pair: xx, xy, yy, zz real; xz, yz are -i t.
+// GLOBAL: tp points into the tensor in global memory (read-only path),
+// otherwise into the shared-memory copy of the CTA's tensor slice.
+template <typename T, typename C, bool GLOBAL>
+__device__ __forceinline__ void layer_mac(const T* __restrict__ tp, long tc, const C& vx, const C& vy, const C& vz,
+                                          T& axr, T& axi, T& ayr, T& ayi, T& azr, T& azi) {
+    T txx, txy, txz, tyy, tyz, tzz;
+    if constexpr (GLOBAL) {
+        txx = __ldg(tp); txy = __ldg(tp + tc); txz = __ldg(tp + 2 * tc);
+        tyy = __ldg(tp + 3 * tc); tyz = __ldg(tp + 4 * tc); tzz = __ldg(tp + 5 * tc);
+    } else {
+        txx = tp[0]; txy = tp[tc]; txz = tp[2 * tc]; tyy = tp[3 * tc]; tyz = tp[4 * tc]; tzz = tp[5 * tc];
+    }
+    // (-i t)(a + i b) = t b - i t a
+    axr += txx * vx.x + txy * vy.x + txz * vz.y;
+    axi += txx * vx.y + txy * vy.y - txz * vz.x;
+    ayr += txy * vx.x + tyy * vy.x + tyz * vz.y;
+    ayi += txy * vx.y + tyy * vy.y - tyz * vz.x;
+    azr += txz * vx.y + tyz * vy.y + tzz * vz.x;
+    azi += tzz * vz.y - txz * vx.x - tyz * vy.x;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kLayCols * kLayRows)
 p3_layers(DemagDims d, typename Cplx<T>::type* __restrict__ S, const T* __restrict__ tens) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);      // [3 nz][kLayCols]
     const int nz = d.nz, LY = d.LY, KY2 = LY / 2 + 1;
+    C* sP = reinterpret_cast<C*>(smraw);          // [nz][3][kLayCols]: P_j
+    C* sQ = sP + 3 * nz * kLayCols;               // [nz][3][kLayCols]: Q_j
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int kx = blockIdx.x * kLayCols + tx;
     const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
@@ -893,36 +923,126 @@ p3_layers(DemagDims d, typename Cplx<T>::type* __restrict__ S, const T* __restri
     const int ky = side ? LY - p : p;
     const long zs = (long)LY * d.KXS;                       // one (component, layer) plane
     C* col = S + (long)blockIdx.z * 3 * nz * zs + (long)ky * d.KXS + kx;
-    for (int q = ty; q < 3 * nz; q += kLayRows) sm[q * kLayCols + tx] = valid ? col[q * zs] : mk<C>(0, 0);
+    const T* lh = static_cast<const T*>(d.lh);
+    const T e = side ? (T)-1 : (T)1;
+    for (int q = ty; q < 3 * nz; q += kLayRows) {
+        const int c = q / nz, j = q - c * nz;
+        C v = valid ? col[q * zs] : mk<C>(0, 0);
+        if (c == 1) { v.x *= e; v.y *= e; }
+        const T w = (c == 2 ? -lh[j] : lh[j]);
+        sP[(j * 3 + c) * kLayCols + tx] = v;
+        sQ[(j * 3 + c) * kLayCols + tx] = mk<C>(w * v.x, w * v.y);
+    }
     __syncthreads();
     if (!valid) return;
-    const T sy = side ? (T)-1 : (T)1;                       // odd in y: xy, yz
     const long prow = (long)KY2 * d.KXS;                    // one pair
     const long tc = (long)(nz * (nz + 1) / 2) * prow;       // one component
     const T* t0 = tens + (long)p * d.KXS + kx;
-    const T* lh = static_cast<const T*>(d.lh);
     for (int i = ty; i < nz; i += kLayRows) {
-        const T hi = lh[i];
-        T hxr = 0, hxi = 0, hyr = 0, hyi = 0, hzr = 0, hzi = 0;
-        for (int j = 0; j < nz; ++j) {
-            const bool lo = i <= j;
-            const T* tp = t0 + (long)(lo ? layer_pair(i, j, nz) : layer_pair(j, i, nz)) * prow;
-            const T r = lo ? (T)1 : lh[j] / hi;
-            const T so = lo ? r : -r;                          // K(-k) flips the single-odd components
-            const T txx = r * __ldg(tp), txy = r * sy * __ldg(tp + tc), txz = so * __ldg(tp + 2 * tc);
-            const T tyy = r * __ldg(tp + 3 * tc), tyz = so * sy * __ldg(tp + 4 * tc), tzz = r * __ldg(tp + 5 * tc);
-            const C mx = sm[j * kLayCols + tx], my = sm[(nz + j) * kLayCols + tx], mz = sm[(2 * nz + j) * kLayCols + tx];
-            // xz and yz are -i t: (-i t)(a + i b) = t b - i t a
-            hxr += txx * mx.x + txy * my.x + txz * mz.y;
-            hxi += txx * mx.y + txy * my.y - txz * mz.x;
-            hyr += txy * mx.x + tyy * my.x + tyz * mz.y;
-            hyi += txy * mx.y + tyy * my.y - tyz * mz.x;
-            hzr += txz * mx.y + tyz * my.y + tzz * mz.x;
-            hzi += -txz * mx.x - tyz * my.x + tzz * mz.y;
+        T axr = 0, axi = 0, ayr = 0, ayi = 0, azr = 0, azi = 0;
+        {   // j >= i: pairs q(i, i) .. q(i, nz - 1) are consecutive
+            const T* tp = t0 + (long)layer_pair(i, i, nz) * prow;
+#pragma unroll 1
+            for (int j = i; j < nz; ++j, tp += prow) {
+                const C* v = sP + j * 3 * kLayCols + tx;
+                layer_mac<T, C, true>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], axr, axi, ayr, ayi, azr, azi);
+            }
         }
-        col[(long)i * zs] = mk<C>(hxr, hxi);
-        col[(long)(nz + i) * zs] = mk<C>(hyr, hyi);
-        col[(long)(2 * nz + i) * zs] = mk<C>(hzr, hzi);
+        T bxr = 0, bxi = 0, byr = 0, byi = 0, bzr = 0, bzi = 0;
+        {   // j < i: pair q(j, i); q(j + 1, i) - q(j, i) = nz - j - 1
+            const T* tp = t0 + (long)i * prow;              // q(0, i) = i
+#pragma unroll 1
+            for (int j = 0; j < i; ++j) {
+                const C* v = sQ + j * 3 * kLayCols + tx;
+                layer_mac<T, C, true>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], bxr, bxi, byr, byi, bzr, bzi);
+                tp += (long)(nz - j - 1) * prow;
+            }
+        }
+        const T ih = (T)1 / lh[i];
+        const T cz = -ih;                                   // D on the lower-triangle sum
+        col[(long)i * zs] = mk<C>(axr + ih * bxr, axi + ih * bxi);
+        col[(long)(nz + i) * zs] = mk<C>(e * (ayr + ih * byr), e * (ayi + ih * byi));
+        col[(long)(2 * nz + i) * zs] = mk<C>(azr + cz * bzr, azi + cz * bzi);
+    }
+}
+
+// The same coupling with the CTA's whole tensor slice (6 components x all
+// stored pairs x 32 columns of row p) staged in shared memory by one TMA copy
+// issued before the inputs are loaded, so the CTA waits for memory once
+// instead of once per layer pair.  For stacks whose slice fits (6 npair <= 256
+// rows per box dimension, shared memory permitting).  The wait is bounded: on
+// timeout the CTA records kErrTmaTimeout, waits (bounded) once more for its
+// copy and leaves.
+template <typename T>
+__global__ void __launch_bounds__(kLayCols * kLayRows)
+p3_layers_tma(DemagDims d, const __grid_constant__ CUtensorMap tmap, typename Cplx<T>::type* __restrict__ S) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    const int nz = d.nz, LY = d.LY;
+    const int npair = nz * (nz + 1) / 2;
+    T* sT = reinterpret_cast<T*>(smtma);                                   // [6][npair][kLayCols]
+    C* sP = reinterpret_cast<C*>(sT + 6 * npair * kLayCols);              // [nz][3][kLayCols]
+    C* sQ = sP + 3 * nz * kLayCols;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + 3 * nz * kLayCols);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kLayCols + tx;
+    const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
+    const bool row_ok = p < LY / 2 + 1 && (side == 0 || (p > 0 && 2 * p < LY));
+    if (!row_ok) return;                    // uniform over the CTA: nothing issued yet
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(bar, (uint32_t)(6 * npair * kLayCols * sizeof(T)));
+        tma_load_4d(sT, &tmap, bar, blockIdx.x * kLayCols, p, 0, 0);
+    }
+    const int kx = blockIdx.x * kLayCols + tx;
+    const bool valid = kx < d.KX;
+    const int ky = side ? LY - p : p;
+    const long zs = (long)LY * d.KXS;
+    C* col = S + (long)ky * d.KXS + kx;
+    const T* lh = static_cast<const T*>(d.lh);
+    const T e = side ? (T)-1 : (T)1;
+    for (int q = ty; q < 3 * nz; q += kLayRows) {
+        const int c = q / nz, j = q - c * nz;
+        C v = valid ? col[q * zs] : mk<C>(0, 0);
+        if (c == 1) { v.x *= e; v.y *= e; }
+        const T w = (c == 2 ? -lh[j] : lh[j]);
+        sP[(j * 3 + c) * kLayCols + tx] = v;
+        sQ[(j * 3 + c) * kLayCols + tx] = mk<C>(w * v.x, w * v.y);
+    }
+    __syncthreads();                        // the barrier's init is visible to every waiting thread
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(d.err, kErrTmaTimeout);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    if (!valid) return;
+    const long tc = (long)npair * kLayCols;
+    for (int i = ty; i < nz; i += kLayRows) {
+        T axr = 0, axi = 0, ayr = 0, ayi = 0, azr = 0, azi = 0;
+        {
+            const T* tp = sT + (long)layer_pair(i, i, nz) * kLayCols + tx;
+            for (int j = i; j < nz; ++j, tp += kLayCols) {
+                const C* v = sP + j * 3 * kLayCols + tx;
+                layer_mac<T, C, false>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], axr, axi, ayr, ayi, azr, azi);
+            }
+        }
+        T bxr = 0, bxi = 0, byr = 0, byi = 0, bzr = 0, bzi = 0;
+        {
+            const T* tp = sT + (long)i * kLayCols + tx;
+            for (int j = 0; j < i; ++j) {
+                const C* v = sQ + j * 3 * kLayCols + tx;
+                layer_mac<T, C, false>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], bxr, bxi, byr, byi, bzr, bzi);
+                tp += (long)(nz - j - 1) * kLayCols;
+            }
+        }
+        const T ih = (T)1 / lh[i];
+        const T cz = -ih;
+        col[(long)i * zs] = mk<C>(axr + ih * bxr, axi + ih * bxi);
+        col[(long)(nz + i) * zs] = mk<C>(e * (ayr + ih * byr), e * (ayi + ih * byi));
+        col[(long)(2 * nz + i) * zs] = mk<C>(azr + cz * bzr, azi + cz * bzi);
     }
 }
 
@@ -1483,9 +1603,34 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
 // P2 .. P4: S1 -> S1 through the tensor multiply.  A 2-D grid (nz = 1, Py <= 256)
 // runs the z-pass kernel along y in place on S1 instead (one pass, no S2).
 template <typename T>
+static bool launch_p3_layers_tma(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    const int npair = d.nz * (d.nz + 1) / 2;
+    if (!d.err || d.nb != 1 || npair > 256 || (d.KXS * sizeof(T)) % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(tens) & 15) != 0)
+        return false;
+    const size_t sm = (size_t)6 * npair * kLayCols * sizeof(T) + (size_t)2 * 3 * d.nz * kLayCols * sizeof(C) + 16;
+    if (sm > 200 * 1024) return false;
+    const int KY2 = d.LY / 2 + 1;
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)d.KX, (cuuint64_t)KY2, (cuuint64_t)npair, 6};
+    const cuuint64_t strides[3] = {(cuuint64_t)d.KXS * sizeof(T), (cuuint64_t)KY2 * d.KXS * sizeof(T),
+                                   (cuuint64_t)npair * KY2 * d.KXS * sizeof(T)};
+    const cuuint32_t box[4] = {(cuuint32_t)kLayCols, 1, (cuuint32_t)npair, 6};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (!encode_4d(&map, dt, tens, dims, strides, box)) return false;
+    auto k = p3_layers_tma<T>;
+    set_smem(k, sm);
+    dim3 grid((d.KX + kLayCols - 1) / kLayCols, 2 * KY2, 1);
+    k<<<grid, dim3(kLayCols, kLayRows), sm, st>>>(d, map, S2);
+    return true;
+}
+
+template <typename T>
 static void launch_p3_layers(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens, cudaStream_t st) {
     using C = typename Cplx<T>::type;
-    const size_t sm = (size_t)3 * d.nz * kLayCols * sizeof(C);
+    if (launch_p3_layers_tma<T>(d, S2, tens, st)) return;
+    const size_t sm = (size_t)2 * 3 * d.nz * kLayCols * sizeof(C);
     auto k = p3_layers<T>;
     set_smem(k, sm);
     dim3 grid((d.KX + kLayCols - 1) / kLayCols, 2 * (d.LY / 2 + 1), d.nb);

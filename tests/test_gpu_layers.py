@@ -59,6 +59,22 @@ def test_layers_field_and_energy(n, precision):
     s.close()
 
 
+@pytest.mark.parametrize("n,precision", [((10, 6, 16), "fp64"), ((10, 6, 16), "fp32"), ((8, 5, 22), "fp32")])
+def test_many_layers(n, precision):
+    """Stacks whose tensor slice no longer fits one shared-memory copy (16
+    layers in FP64, 22 in FP32) take the register-fed coupling kernel; 16
+    layers in FP32 still the staged one."""
+    from paper_2302_08843_gb300.workloads import from_soa
+    w, s, prob = _setup(n, precision)
+    h, E = s.heff(energies=True)
+    assert rel(from_soa(to_host(h)), prob.heff(w.m0, 0.0)) < _tol(precision, w)
+    Eref = prob.energies(w.m0, 0.0)
+    Escale = max(abs(e) for e in Eref)
+    for a, b in zip(E, Eref):
+        assert abs(a - b) < _tol(precision, w) * Escale, (E, Eref)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_layers_demag_alone(precision):
     """Exchange, anisotropy and field off: the demag term alone (the coupling pass)."""
