@@ -966,48 +966,60 @@ p3_layers(DemagDims d, typename Cplx<T>::type* __restrict__ S, const T* __restri
     }
 }
 
-// The same coupling with the CTA's whole tensor slice (6 components x all
-// stored pairs x 32 columns of row p) staged in shared memory by one TMA copy
-// issued before the inputs are loaded, so the CTA waits for memory once
-// instead of once per layer pair.  For stacks whose slice fits (6 npair <= 256
-// rows per box dimension, shared memory permitting).  The wait is bounded: on
-// timeout the CTA records kErrTmaTimeout, waits (bounded) once more for its
-// copy and leaves.
+// The same coupling with everything a CTA reads staged in shared memory by
+// TMA in one round trip: the tensor slice of row p (6 components x all stored
+// pairs x 32 columns) and the 3 nz input planes of the 32 columns for both
+// rows that share the slice, ky = p and its mirror ky = Py - p.  Every staged
+// tensor entry is read once and applied to both rows.  For stacks whose slice
+// fits (npair <= 256 and 3 nz <= 256 per box dimension, shared memory
+// permitting).  The wait is bounded: on timeout the CTA records
+// kErrTmaTimeout, waits (bounded) once more for its copies and leaves.
+template <typename T, typename C>
+__device__ __forceinline__ void layer_fma(const T (&t)[6], const C* v, int ps, T (&a)[6]) {
+    const C vx = v[0], vy = v[ps], vz = v[2 * ps];
+    // xx, xy, yy, zz real; xz, yz are -i t: (-i t)(a + i b) = t b - i t a
+    a[0] += t[0] * vx.x + t[1] * vy.x + t[2] * vz.y;
+    a[1] += t[0] * vx.y + t[1] * vy.y - t[2] * vz.x;
+    a[2] += t[1] * vx.x + t[3] * vy.x + t[4] * vz.y;
+    a[3] += t[1] * vx.y + t[3] * vy.y - t[4] * vz.x;
+    a[4] += t[2] * vx.y + t[4] * vy.y + t[5] * vz.x;
+    a[5] += t[5] * vz.y - t[2] * vx.x - t[4] * vy.x;
+}
+
+// h^_i = E [A + (1 / h_i) D B] written to the column's three planes of layer i
+template <typename T, typename C>
+__device__ __forceinline__ void layer_store(C* col, long zs, int nz, int i, T ih, T e, const T (&a)[6],
+                                            const T (&b)[6]) {
+    col[(long)i * zs] = mk<C>(a[0] + ih * b[0], a[1] + ih * b[1]);
+    col[(long)(nz + i) * zs] = mk<C>(e * (a[2] + ih * b[2]), e * (a[3] + ih * b[3]));
+    col[(long)(2 * nz + i) * zs] = mk<C>(a[4] - ih * b[4], a[5] - ih * b[5]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kLayCols * kLayRows)
-p3_layers_tma(DemagDims d, const __grid_constant__ CUtensorMap tmap, typename Cplx<T>::type* __restrict__ S) {
+p3_layers_tma(DemagDims d, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap smap,
+              typename Cplx<T>::type* __restrict__ S) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smtma[];
     const int nz = d.nz, LY = d.LY;
     const int npair = nz * (nz + 1) / 2;
+    const int pl = 3 * nz * kLayCols;                                      // one row's planes
     T* sT = reinterpret_cast<T*>(smtma);                                   // [6][npair][kLayCols]
-    C* sP = reinterpret_cast<C*>(sT + 6 * npair * kLayCols);              // [nz][3][kLayCols]
-    C* sQ = sP + 3 * nz * kLayCols;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + 3 * nz * kLayCols);
+    C* sP = reinterpret_cast<C*>(sT + 6 * npair * kLayCols);              // [row][c nz + j][kLayCols]
+    C* sQ = sP + 2 * pl;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + 2 * pl);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kLayCols + tx;
-    const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
-    const bool row_ok = p < LY / 2 + 1 && (side == 0 || (p > 0 && 2 * p < LY));
-    if (!row_ok) return;                    // uniform over the CTA: nothing issued yet
+    const int p = blockIdx.y;
+    const bool two = p > 0 && 2 * p < LY;                                  // a distinct mirrored row
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
-        mbar_arrive_expect_tx(bar, (uint32_t)(6 * npair * kLayCols * sizeof(T)));
+        const uint32_t tb = (uint32_t)(6 * npair * kLayCols * sizeof(T)), mb = (uint32_t)(pl * sizeof(C));
+        mbar_arrive_expect_tx(bar, tb + (two ? 2 : 1) * mb);
         tma_load_4d(sT, &tmap, bar, blockIdx.x * kLayCols, p, 0, 0);
-    }
-    const int kx = blockIdx.x * kLayCols + tx;
-    const bool valid = kx < d.KX;
-    const int ky = side ? LY - p : p;
-    const long zs = (long)LY * d.KXS;
-    C* col = S + (long)ky * d.KXS + kx;
-    const T* lh = static_cast<const T*>(d.lh);
-    const T e = side ? (T)-1 : (T)1;
-    for (int q = ty; q < 3 * nz; q += kLayRows) {
-        const int c = q / nz, j = q - c * nz;
-        C v = valid ? col[q * zs] : mk<C>(0, 0);
-        if (c == 1) { v.x *= e; v.y *= e; }
-        const T w = (c == 2 ? -lh[j] : lh[j]);
-        sP[(j * 3 + c) * kLayCols + tx] = v;
-        sQ[(j * 3 + c) * kLayCols + tx] = mk<C>(w * v.x, w * v.y);
+        const int xw = blockIdx.x * kLayCols * (int)(sizeof(C) / 8);       // 8-byte elements
+        tma_load_3d(sP, &smap, bar, xw, p, 0);
+        if (two) tma_load_3d(sP + pl, &smap, bar, xw, LY - p, 0);
     }
     __syncthreads();                        // the barrier's init is visible to every waiting thread
     const bool ok = mbar_wait_bounded(bar, 0);
@@ -1018,31 +1030,41 @@ p3_layers_tma(DemagDims d, const __grid_constant__ CUtensorMap tmap, typename Cp
         }
         return;
     }
-    if (!valid) return;
-    const long tc = (long)npair * kLayCols;
-    for (int i = ty; i < nz; i += kLayRows) {
-        T axr = 0, axi = 0, ayr = 0, ayi = 0, azr = 0, azi = 0;
-        {
-            const T* tp = sT + (long)layer_pair(i, i, nz) * kLayCols + tx;
-            for (int j = i; j < nz; ++j, tp += kLayCols) {
-                const C* v = sP + j * 3 * kLayCols + tx;
-                layer_mac<T, C, false>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], axr, axi, ayr, ayi, azr, azi);
-            }
+    // P = E M (E on the mirrored row), Q = h_j D P, each thread on its own column
+    const T* lh = static_cast<const T*>(d.lh);
+    for (int side = 0; side < (two ? 2 : 1); ++side)
+        for (int q = ty; q < 3 * nz; q += kLayRows) {
+            const int c = q >= 2 * nz ? 2 : (q >= nz ? 1 : 0), j = q - c * nz;
+            C v = sP[side * pl + q * kLayCols + tx];
+            if (side && c == 1) { v.x = -v.x; v.y = -v.y; sP[side * pl + q * kLayCols + tx] = v; }
+            const T w = c == 2 ? -lh[j] : lh[j];
+            sQ[side * pl + q * kLayCols + tx] = mk<C>(w * v.x, w * v.y);
         }
-        T bxr = 0, bxi = 0, byr = 0, byi = 0, bzr = 0, bzi = 0;
-        {
-            const T* tp = sT + (long)i * kLayCols + tx;
-            for (int j = 0; j < i; ++j) {
-                const C* v = sQ + j * 3 * kLayCols + tx;
-                layer_mac<T, C, false>(tp, tc, v[0], v[kLayCols], v[2 * kLayCols], bxr, bxi, byr, byi, bzr, bzi);
-                tp += (long)(nz - j - 1) * kLayCols;
-            }
+    __syncthreads();
+    const int kx = blockIdx.x * kLayCols + tx;
+    if (kx >= d.KX) return;
+    const long zs = (long)LY * d.KXS;
+    const long tc = (long)npair * kLayCols;
+    const int ps = nz * kLayCols;
+    for (int i = ty; i < nz; i += kLayRows) {
+        T a0[6] = {0, 0, 0, 0, 0, 0}, a1[6] = {0, 0, 0, 0, 0, 0};
+        T b0[6] = {0, 0, 0, 0, 0, 0}, b1[6] = {0, 0, 0, 0, 0, 0};
+        const T* tp = sT + (long)layer_pair(i, i, nz) * kLayCols + tx;    // j >= i: consecutive pairs
+        for (int j = i; j < nz; ++j, tp += kLayCols) {
+            const T t[6] = {tp[0], tp[tc], tp[2 * tc], tp[3 * tc], tp[4 * tc], tp[5 * tc]};
+            layer_fma<T, C>(t, sP + j * kLayCols + tx, ps, a0);
+            if (two) layer_fma<T, C>(t, sP + pl + j * kLayCols + tx, ps, a1);
+        }
+        tp = sT + (long)i * kLayCols + tx;                                // j < i: pair q(j, i)
+        for (int j = 0; j < i; ++j) {
+            const T t[6] = {tp[0], tp[tc], tp[2 * tc], tp[3 * tc], tp[4 * tc], tp[5 * tc]};
+            layer_fma<T, C>(t, sQ + j * kLayCols + tx, ps, b0);
+            if (two) layer_fma<T, C>(t, sQ + pl + j * kLayCols + tx, ps, b1);
+            tp += (long)(nz - j - 1) * kLayCols;
         }
         const T ih = (T)1 / lh[i];
-        const T cz = -ih;
-        col[(long)i * zs] = mk<C>(axr + ih * bxr, axi + ih * bxi);
-        col[(long)(nz + i) * zs] = mk<C>(e * (ayr + ih * byr), e * (ayi + ih * byi));
-        col[(long)(2 * nz + i) * zs] = mk<C>(azr + cz * bzr, azi + cz * bzi);
+        layer_store<T, C>(S + (long)p * d.KXS + kx, zs, nz, i, ih, (T)1, a0, b0);
+        if (two) layer_store<T, C>(S + (long)(LY - p) * d.KXS + kx, zs, nz, i, ih, (T)-1, a1, b1);
     }
 }
 
@@ -1606,23 +1628,29 @@ template <typename T>
 static bool launch_p3_layers_tma(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens, cudaStream_t st) {
     using C = typename Cplx<T>::type;
     const int npair = d.nz * (d.nz + 1) / 2;
-    if (!d.err || d.nb != 1 || npair > 256 || (d.KXS * sizeof(T)) % 16 != 0 ||
-        (reinterpret_cast<uintptr_t>(tens) & 15) != 0)
+    if (!d.err || d.nb != 1 || npair > 256 || 3 * d.nz > 256 || (d.KXS * sizeof(T)) % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(tens) & 15) != 0 || (reinterpret_cast<uintptr_t>(S2) & 15) != 0)
         return false;
-    const size_t sm = (size_t)6 * npair * kLayCols * sizeof(T) + (size_t)2 * 3 * d.nz * kLayCols * sizeof(C) + 16;
+    const size_t sm = (size_t)6 * npair * kLayCols * sizeof(T) + (size_t)4 * 3 * d.nz * kLayCols * sizeof(C) + 16;
     if (sm > 200 * 1024) return false;
     const int KY2 = d.LY / 2 + 1;
-    CUtensorMap map;
-    const cuuint64_t dims[4] = {(cuuint64_t)d.KX, (cuuint64_t)KY2, (cuuint64_t)npair, 6};
-    const cuuint64_t strides[3] = {(cuuint64_t)d.KXS * sizeof(T), (cuuint64_t)KY2 * d.KXS * sizeof(T),
-                                   (cuuint64_t)npair * KY2 * d.KXS * sizeof(T)};
-    const cuuint32_t box[4] = {(cuuint32_t)kLayCols, 1, (cuuint32_t)npair, 6};
+    CUtensorMap tmap, smap;
+    const cuuint64_t tdims[4] = {(cuuint64_t)d.KX, (cuuint64_t)KY2, (cuuint64_t)npair, 6};
+    const cuuint64_t tstrides[3] = {(cuuint64_t)d.KXS * sizeof(T), (cuuint64_t)KY2 * d.KXS * sizeof(T),
+                                    (cuuint64_t)npair * KY2 * d.KXS * sizeof(T)};
+    const cuuint32_t tbox[4] = {(cuuint32_t)kLayCols, 1, (cuuint32_t)npair, 6};
     const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    if (!encode_4d(&map, dt, tens, dims, strides, box)) return false;
+    if (!encode_4d(&tmap, dt, tens, tdims, tstrides, tbox)) return false;
+    // the spectrum as 8-byte elements: (KX complex columns, Py rows, 3 nz planes)
+    constexpr int W8 = (int)(sizeof(C) / 8);
+    const cuuint64_t sdims[3] = {(cuuint64_t)d.KX * W8, (cuuint64_t)d.LY, (cuuint64_t)(3 * d.nz)};
+    const cuuint64_t sstrides[2] = {(cuuint64_t)d.KXS * sizeof(C), (cuuint64_t)d.LY * d.KXS * sizeof(C)};
+    const cuuint32_t sbox[3] = {(cuuint32_t)(kLayCols * W8), 1, (cuuint32_t)(3 * d.nz)};
+    if (!encode_3d(&smap, S2, sdims, sstrides, sbox)) return false;
     auto k = p3_layers_tma<T>;
     set_smem(k, sm);
-    dim3 grid((d.KX + kLayCols - 1) / kLayCols, 2 * KY2, 1);
-    k<<<grid, dim3(kLayCols, kLayRows), sm, st>>>(d, map, S2);
+    dim3 grid((d.KX + kLayCols - 1) / kLayCols, KY2, 1);
+    k<<<grid, dim3(kLayCols, kLayRows), sm, st>>>(d, tmap, smap, S2);
     return true;
 }
 
