@@ -168,21 +168,34 @@ class ClockSampler:
 # ---------------------------------------------------------- CPU baseline --
 def _oracle_sample(result_path, n_stages, crop):
     """Time RK stages of the unmodified oracle on the bulk workload (or a crop
-    of the same construction).  Runs in a spawned process."""
+    of the same construction), then three stages of each small configuration
+    (plain 32x32x4, thin film 512x128x1, multilayer crop 64x64x8).  Runs in a
+    spawned process."""
     sys.path.insert(0, ROOT)
-    import numpy as np
     from oracle.llg import Problem
     from paper_2302_08843_gb300 import workloads as W
+
+    def stages(w, n, **kw):
+        prob = Problem(w.n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, Ku1=w.Ku1, ku_axis=w.ku_axis_cells(),
+                       h_ext=w.h_ext(0.0) if callable(w.h_ext) else w.h_ext, **kw)
+        m = w.m0
+        t0 = time.perf_counter()
+        for s in range(n):
+            k = prob.rhs(m, s * w.dt)
+            m = m + 0.5 * w.dt * k
+        return time.perf_counter() - t0
+
     w = W.bulk(crop=crop)
-    prob = Problem(w.n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, Ku1=w.Ku1, ku_axis=w.ku_axis_cells(),
-                   h_ext=w.h_ext)
-    m = w.m0
-    t0 = time.perf_counter()
-    for s in range(n_stages):
-        k = prob.rhs(m, s * w.dt)
-        m = m + 0.5 * w.dt * k
-    el = time.perf_counter() - t0
-    json.dump({"seconds": el, "stages": n_stages, "cells": w.ncells, "n": list(w.n)}, open(result_path, "w"))
+    el = stages(w, n_stages)
+    small = {}
+    for name, ws, kw in (("plain_fp64_32x32x4", W.plain_fp64(), {}), ("thin_film_512x128x1", W.thin_film(), {}),
+                         ("multilayer_64x64x8", W.multilayer(n=(64, 64, 8)), None)):
+        if kw is None:
+            kw = {"layers": ws.extra["layers"]}
+        sec = stages(ws, 3, **kw)
+        small[name] = {"cell_updates_per_s": ws.ncells * 3 / sec, "stages": 3, "seconds": round(sec, 3)}
+    json.dump({"seconds": el, "stages": n_stages, "cells": w.ncells, "n": list(w.n), "small": small},
+              open(result_path, "w"))
 
 
 def start_cpu_baseline(n_stages=1, crop=None):
@@ -205,7 +218,7 @@ def finish_cpu_baseline(p, path, sample_desc):
         except OSError:
             pass
     return {"value": r["cells"] * r["stages"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample_desc % r}
+            "sample": sample_desc % r, "small_configs": r.get("small")}
 
 
 # ------------------------------------------------------------------ ours --
@@ -629,7 +642,7 @@ def run_ours(args):
     w.steps = args.steps
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = start_cpu_baseline(n_stages=1)
+        cpu = start_cpu_baseline(n_stages=3)
 
     def barrier():
         if dist is not None:
@@ -674,7 +687,7 @@ def run_ours(args):
     # field callbacks), so they run after it has finished
     cpu_res = None
     if cpu is not None:
-        cpu_res = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stage of the FP64 oracle on the "
+        cpu_res = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stages of the FP64 oracle on the "
                                       "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")
     serving = None
     if args.serve_requests > 0 and not args.nz:

@@ -303,8 +303,9 @@ mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins);
 
 /* Host-only helper (no GPU): the padded FFT extent the library uses along an
  * axis of n cells (Sec. 4.4 zero padding, P >= 2n): 1 for n = 1, otherwise the
- * smallest length >= 2n among the powers of two up to 4096 and the 5-smooth
- * lengths 100, 200, 400 and 800, which the mixed-radix passes transform.
+ * smallest length >= 2n among the powers of two up to 4096 and the lengths
+ * r 2^a the mixed-radix passes transform (r = 3: 96, 192, 384, 768; r = 7:
+ * 112, 224, 448, 896; r = 25: 100, 200, 400, 800).
  * 0 for n < 1. */
 int mm_fft_extent(int n);
 

@@ -142,7 +142,8 @@ def demag_tensor_host(n, dx, p=20):
 
 def padded_extents(n):
     """Padded FFT extent per axis (mm_fft_extent): 1 for a single cell, else the
-    smallest supported length >= 2n (powers of two and 100, 200, 400, 800)."""
+    smallest supported length >= 2n (powers of two and the mixed-radix lengths
+    96, 100, 112, 192, 200, 224, 384, 400, 448, 768, 800, 896)."""
     return tuple(int(lib().mm_fft_extent(int(v))) for v in n)
 
 

@@ -33,8 +33,9 @@ template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
 // translation unit that runs FFTs owns a copy and an upload function).
 static __device__ double2 g_tw64[kMaxFft];
 static __device__ float2 g_tw32[kMaxFft];
-// W5[m] = exp(-2 pi i m / kTw5): twiddles of the 5-smooth lengths (all divide kTw5)
-constexpr int kTw5 = 3200;
+// W5[m] = exp(-2 pi i m / kTw5): twiddles of the mixed-radix lengths r 2^k
+// (r = 3, 7 or 25), all of which divide kTw5 = 2^8 3 5^2 7
+constexpr int kTw5 = 134400;
 static __device__ double2 g_tw5_64[kTw5];
 static __device__ float2 g_tw5_32[kTw5];
 
@@ -150,6 +151,47 @@ template <int DIR, typename C> __device__ __forceinline__ void dft5(C& a0, C& a1
     a4 = csub(t1, iu);
     a2 = cadd(t2, iw);
     a3 = csub(t2, iw);
+}
+
+// DFT3 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 3):
+// X0 = a0 + (a1 + a2), X1,2 = a0 - (a1 + a2) / 2 +- DIR i (sqrt 3 / 2)(a1 - a2)
+template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+    using T = decltype(C::x);
+    constexpr T h = (T)0.86602540378443864676;      // sin(2 pi / 3)
+    const C sm = cadd(a1, a2), df = csub(a1, a2);
+    const C t = mk<C>(a0.x - (T)0.5 * sm.x, a0.y - (T)0.5 * sm.y);
+    const C u = DIR < 0 ? mk<C>(h * df.y, -h * df.x) : mk<C>(-h * df.y, h * df.x);    // DIR i h df
+    a0 = cadd(a0, sm);
+    a1 = cadd(t, u);
+    a2 = csub(t, u);
+}
+
+// DFT7 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 7), from the pairs
+// p_k = a_k + a_{7-k}, m_k = a_k - a_{7-k} (k = 1, 2, 3):
+// X_q, X_{7-q} = a0 + sum_k p_k cos(2 pi k q / 7) +- DIR i sum_k m_k sin(2 pi k q / 7)
+template <int DIR, typename C> __device__ __forceinline__ void dft7(C (&a)[7]) {
+    using T = decltype(C::x);
+    constexpr T c1 = (T)0.62348980185873353053, c2 = (T)-0.22252093395631440429, c3 = (T)-0.90096886790241912624;
+    constexpr T s1 = (T)0.78183148246802980871, s2 = (T)0.97492791218182360702, s3 = (T)0.43388373911755812048;
+    const C p1 = cadd(a[1], a[6]), m1 = csub(a[1], a[6]);
+    const C p2 = cadd(a[2], a[5]), m2 = csub(a[2], a[5]);
+    const C p3 = cadd(a[3], a[4]), m3 = csub(a[3], a[4]);
+    const C a0 = a[0];
+    // cosine parts (kq mod 7 -> cos of the nearer of r, 7 - r)
+    const C t1 = mk<C>(a0.x + c1 * p1.x + c2 * p2.x + c3 * p3.x, a0.y + c1 * p1.y + c2 * p2.y + c3 * p3.y);
+    const C t2 = mk<C>(a0.x + c2 * p1.x + c3 * p2.x + c1 * p3.x, a0.y + c2 * p1.y + c3 * p2.y + c1 * p3.y);
+    const C t3 = mk<C>(a0.x + c3 * p1.x + c1 * p2.x + c2 * p3.x, a0.y + c3 * p1.y + c1 * p2.y + c2 * p3.y);
+    // sine parts (sin of 7 - r is -sin r)
+    const C u1 = mk<C>(s1 * m1.x + s2 * m2.x + s3 * m3.x, s1 * m1.y + s2 * m2.y + s3 * m3.y);
+    const C u2 = mk<C>(s2 * m1.x - s3 * m2.x - s1 * m3.x, s2 * m1.y - s3 * m2.y - s1 * m3.y);
+    const C u3 = mk<C>(s3 * m1.x - s1 * m2.x + s2 * m3.x, s3 * m1.y - s1 * m2.y + s2 * m3.y);
+    const C i1 = DIR < 0 ? mk<C>(u1.y, -u1.x) : mk<C>(-u1.y, u1.x);      // DIR i u
+    const C i2 = DIR < 0 ? mk<C>(u2.y, -u2.x) : mk<C>(-u2.y, u2.x);
+    const C i3 = DIR < 0 ? mk<C>(u3.y, -u3.x) : mk<C>(-u3.y, u3.x);
+    a[0] = mk<C>(a0.x + p1.x + p2.x + p3.x, a0.y + p1.y + p2.y + p3.y);
+    a[1] = cadd(t1, i1); a[6] = csub(t1, i1);
+    a[2] = cadd(t2, i2); a[5] = csub(t2, i2);
+    a[3] = cadd(t3, i3); a[4] = csub(t3, i3);
 }
 
 // cos and sin of pi k / 8, k = 0..15

@@ -19,7 +19,8 @@ inline int fft_extent(int n) {
     const int t = 2 * n;
     int best = 1;
     while (best < t) best <<= 1;
-    const int mixed[4] = {100, 200, 400, 800};
+    // the mixed-radix lengths r 2^a (r = 3, 7, 25) of the FFT engine
+    const int mixed[12] = {96, 100, 112, 192, 200, 224, 384, 400, 448, 768, 800, 896};
     for (int L : mixed)
         if (L >= t && L < best) best = L;
     return best;

@@ -676,8 +676,10 @@ p_y_tma(DemagDims d, const __grid_constant__ CUtensorMap in_map, typename Cplx<T
 
 // ------------------------------------------------------------------ P3 ----
 // resident CTAs asked of the register allocator: 1024 (FP32) or 512 (FP64) threads per SM
-template <typename T> constexpr int p3_min_blocks(int threads) {
-    return (sizeof(T) == 4 ? 1024 : 512) / threads > 1 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1;
+// (mixed-radix lines: one, their three parked components fill shared memory anyway)
+template <typename T, int L = 2> constexpr int p3_min_blocks(int threads) {
+    return !is_pow2(L) ? 1
+           : (sizeof(T) == 4 ? 1024 : 512) / threads > 1 ? (sizeof(T) == 4 ? 1024 : 512) / threads : 1;
 }
 
 // Three shared-memory areas, one per component, each the FFT scratch of its
@@ -688,7 +690,7 @@ template <typename T> constexpr int p3_min_blocks(int threads) {
 // a time, which keeps the kernel at four CTAs per SM.
 template <typename T, int LZ, int B, int G>
 __global__ void __launch_bounds__(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL,
-                                  p3_min_blocks<T>(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL))
+                                  p3_min_blocks<T, LZ>(B * G * Fft<T, LZ, -1, (LZ > 1)>::TPL))
 p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restrict__ tens) {
     using C = typename Cplx<T>::type;
     using FF = Fft<T, LZ, -1, (LZ > 1)>;
@@ -715,7 +717,7 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
     C* col = S2 + (long)blockIdx.z * 3 * cstride + (long)ky * d.KXS + kx;   // (c, z) at col[c*cstride + z*LY*KXS]
     const long zs = (long)LY * d.KXS;
 
-    {   // all loads in flight together, parked at this thread's own (pattern) positions
+    if constexpr (NR <= 16) {   // all loads in flight together, parked at this thread's own (pattern) positions
         C in[3][NR];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -729,6 +731,15 @@ p3_z_conv(DemagDims d, typename Cplx<T>::type* __restrict__ S2, const T* __restr
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 if (FF::in_live(r)) area[c][(j + r * TPL) * NL + line] = in[c][r];
+    } else {                    // long mixed-radix lines: straight to shared memory, one component at a time
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int z = FF::in_index(j, r);
+                if (FF::in_live(r))
+                    area[c][(j + r * TPL) * NL + line] = (valid && z < d.nz) ? col[c * cstride + z * zs] : mk<C>(0, 0);
+            }
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
@@ -1285,6 +1296,21 @@ template <typename T, int L> constexpr int b_of() {
 template <typename T, int L> constexpr int g_of() {
     return (b_of<T, L>() * tpl_of<T, L>() >= 256) ? 1 : 256 / (b_of<T, L>() * tpl_of<T, L>());
 }
+// the shared-memory z pass parks three components of every line: keep its
+// B x G lines within 200 KB (long FP64 lines take fewer columns per CTA)
+constexpr size_t kP3Smem = 200 * 1024;
+template <typename T, int L> constexpr int b_p3() {
+    return (size_t)3 * L * b_of<T, L>() * sizeof(typename Cplx<T>::type) <= kP3Smem
+               ? b_of<T, L>()
+               : ((int)(kP3Smem / ((size_t)3 * L * sizeof(typename Cplx<T>::type))) < 1
+                      ? 1 : (int)(kP3Smem / ((size_t)3 * L * sizeof(typename Cplx<T>::type))));
+}
+template <typename T, int L> constexpr int g_p3() {
+    return (size_t)3 * L * b_p3<T, L>() * g_of<T, L>() * sizeof(typename Cplx<T>::type) <= kP3Smem
+               ? g_of<T, L>()
+               : ((int)(kP3Smem / ((size_t)3 * L * b_p3<T, L>() * sizeof(typename Cplx<T>::type))) < 1
+                      ? 1 : (int)(kP3Smem / ((size_t)3 * L * b_p3<T, L>() * sizeof(typename Cplx<T>::type))));
+}
 
 // raise a kernel's dynamic shared-memory limit when the request comes near the
 // 48 KB default (kernels may also hold a little static shared memory)
@@ -1515,11 +1541,12 @@ template <int L> static bool launch_p5_tma(const DemagDims& d, const float2* S1,
 
 template <typename T, int L> static void launch_p3(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens,
                                                    cudaStream_t st) {
-    constexpr int B = b_of<T, L>(), G = g_of<T, L>();
+    constexpr int B = b_p3<T, L>(), G = g_p3<T, L>();
     using C = typename Cplx<T>::type;
     const int kyi = 2 * (d.LY / 2 + 1);
     dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G, d.nb);
-    if constexpr (sizeof(T) == 4 && L <= 256) {
+    // the register-resident variant holds 3 NR values per thread: up to 20
+    if constexpr (sizeof(T) == 4 && L <= 256 && Fft<T, L, -1, (L > 1)>::NR <= 20) {
         if constexpr (is_pow2(L)) {
             if (d.nb == 1 && launch_p3_tma<L>(d, S2, tens, st)) return;
         }
@@ -1615,10 +1642,18 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         case 1024: { constexpr int L_ = 1024; CALL; } break; \
         case 2048: { constexpr int L_ = 2048; CALL; } break; \
         case 4096: { constexpr int L_ = 4096; CALL; } break; \
+        case 96: { constexpr int L_ = 96; CALL; } break;     \
         case 100: { constexpr int L_ = 100; CALL; } break;   \
+        case 112: { constexpr int L_ = 112; CALL; } break;   \
+        case 192: { constexpr int L_ = 192; CALL; } break;   \
         case 200: { constexpr int L_ = 200; CALL; } break;   \
+        case 224: { constexpr int L_ = 224; CALL; } break;   \
+        case 384: { constexpr int L_ = 384; CALL; } break;   \
         case 400: { constexpr int L_ = 400; CALL; } break;   \
+        case 448: { constexpr int L_ = 448; CALL; } break;   \
+        case 768: { constexpr int L_ = 768; CALL; } break;   \
         case 800: { constexpr int L_ = 800; CALL; } break;   \
+        case 896: { constexpr int L_ = 896; CALL; } break;   \
         default: break;                     \
     }
 

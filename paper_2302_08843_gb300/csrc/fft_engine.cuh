@@ -239,23 +239,26 @@ struct FftLine16 {
 };
 
 // ------------------------------------------------------------------------
-// Mixed-radix engine for the 5-smooth lengths L = 5^b 2^a (L divides kTw5):
-// radix-5 passes, then radix-4 passes and at most one radix-2 pass, Stockham
-// ordering.  Every pass keeps the line in shared memory: a thread reads its
-// butterflies' inputs (stride L/R), applies the twiddles W_{Ns R}^(q k),
-// transforms them and writes the outputs to their autosorted places.  The
-// register layout at entry and exit and the calling convention are those of
-// FftLine (register r of thread j holds element j + r TPL), so the same
-// kernels drive it; TPL is the largest thread count that divides L/R for
-// every radix R of the plan.
-__host__ __device__ constexpr int m5_fives(int L) { return L % 5 ? 0 : 1 + m5_fives(L / 5); }
-__host__ __device__ constexpr int m5_pow5(int b) { return b == 0 ? 1 : 5 * m5_pow5(b - 1); }
-__host__ __device__ constexpr int m5_twos(int L) { return ilog2(L / m5_pow5(m5_fives(L))); }
+// Mixed-radix engine for the lengths L = r 2^a with r = 3, 7 or 25 (L
+// divides kTw5): passes of the odd radix (3, 7, or 5 twice), then radix-4
+// passes and at most one radix-2 pass, Stockham ordering.  Every pass keeps
+// the line in shared memory: a thread reads its butterflies' inputs (stride
+// L/R), applies the twiddles W_{Ns R}^(q k), transforms them and writes the
+// outputs to their autosorted places.  The register layout at entry and exit
+// and the calling convention are those of FftLine (register r of thread j
+// holds element j + r TPL), so the same kernels drive it; TPL is the largest
+// thread count that divides L/R for every radix R of the plan.
+__host__ __device__ constexpr int m5_oddr(int L) { return L % 3 == 0 ? 3 : (L % 7 == 0 ? 7 : 5); }
+__host__ __device__ constexpr int m5_fives(int L, int r = 0) {
+    return L % (r ? r : m5_oddr(L)) ? 0 : 1 + m5_fives(L / (r ? r : m5_oddr(L)), r ? r : m5_oddr(L));
+}
+__host__ __device__ constexpr int m5_powr(int r, int b) { return b == 0 ? 1 : r * m5_powr(r, b - 1); }
+__host__ __device__ constexpr int m5_twos(int L) { return ilog2(L / m5_powr(m5_oddr(L), m5_fives(L))); }
 __host__ __device__ constexpr int m5_npass(int L) {
     return m5_fives(L) + m5_twos(L) / 2 + m5_twos(L) % 2;
 }
 __host__ __device__ constexpr int m5_radix(int L, int p) {
-    return p < m5_fives(L) ? 5 : (p < m5_fives(L) + m5_twos(L) / 2 ? 4 : 2);
+    return p < m5_fives(L) ? m5_oddr(L) : (p < m5_fives(L) + m5_twos(L) / 2 ? 4 : 2);
 }
 __host__ __device__ constexpr int m5_gcd(int a, int b) { return b == 0 ? a : m5_gcd(b, a % b); }
 __host__ __device__ constexpr int m5_tpl(int L, int p = 0) {
@@ -265,7 +268,7 @@ __host__ __device__ constexpr int m5_tpl(int L, int p = 0) {
 template <typename T, int L, int DIR, bool ZIN>
 struct FftMixed {
     using C = typename Cplx<T>::type;
-    static_assert(kTw5 % L == 0, "5-smooth lengths must divide the twiddle table");
+    static_assert(kTw5 % L == 0, "mixed-radix lengths must divide the twiddle table");
     static constexpr int NP = m5_npass(L);
     static constexpr int TPL = m5_tpl(L);
     static constexpr int NR = L / TPL;
@@ -291,8 +294,10 @@ struct FftMixed {
 #pragma unroll
                 for (int q = 1; q < R; ++q) a[t][q] = cmul(a[t][q], twiddle5<T, DIR>(q * k * (kTw5 / (NS * R))));
             }
-            if constexpr (R == 5) dft5<DIR>(a[t][0], a[t][1], a[t][2], a[t][3], a[t][4]);
+            if constexpr (R == 7) dft7<DIR>(a[t]);
+            else if constexpr (R == 5) dft5<DIR>(a[t][0], a[t][1], a[t][2], a[t][3], a[t][4]);
             else if constexpr (R == 4) dft4<DIR>(a[t][0], a[t][1], a[t][2], a[t][3]);
+            else if constexpr (R == 3) dft3<DIR>(a[t][0], a[t][1], a[t][2]);
             else dft2<DIR>(a[t][0], a[t][1]);
         }
         __syncthreads();
@@ -319,7 +324,7 @@ struct FftMixed {
     }
 };
 
-// engine choice: the mixed-radix engine for 5-smooth lengths, radix 16 for
+// engine choice: the mixed-radix engine for the r 2^a lengths, radix 16 for
 // FP32 power-of-two lines of 16+ points, radix 8 otherwise
 template <typename T, int L, int DIR, bool ZIN>
 using Fft = typename std::conditional<

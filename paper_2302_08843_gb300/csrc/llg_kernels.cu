@@ -47,17 +47,8 @@ __device__ __forceinline__ T thick_harmonic(T a, T b, T ha, T hb) {
     return s != (T)0 ? (ha + hb) * a * b / s : (T)0;
 }
 
-// VEC consecutive cells along x per thread (float4 / double2 loads).
+// VEC consecutive cells along x per thread (float2 / double2 loads).
 template <typename T, int VEC> struct Vec;
-template <> struct Vec<float, 4> {
-    static __device__ __forceinline__ void ld(const float* p, float* v) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-    static __device__ __forceinline__ void st(float* p, const float* v) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
 template <> struct Vec<float, 2> {
     static __device__ __forceinline__ void ld(const float* p, float* v) {
         const float2 q = *reinterpret_cast<const float2*>(p);
@@ -103,8 +94,13 @@ template <typename T> __device__ __forceinline__ void cross_add(const T* e, T wx
     oz += e[0] * wy - e[1] * wx;
 }
 
+// resident CTAs asked of the register allocator: three for FP32 without DMI
+// (a latency-bound kernel; measured 13 % faster than two at 128 registers on
+// a 256x256x8 grid), two otherwise (FP64 is ALU-bound, the DMI variant would spill)
+template <typename T, bool DMI> constexpr int stage_min_blocks() { return (sizeof(T) == 4 && !DMI) ? 3 : 2; }
+
 template <typename T, int VEC, bool UNI, bool DMI>
-__global__ void __launch_bounds__(kStageThreads, 2) stage_kernel(StageParams<T> p) {
+__global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) stage_kernel(StageParams<T> p) {
     using LV = Vec<T, VEC>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N;
@@ -454,7 +450,7 @@ template <typename T> void launch_combine(const T* mn, const T* const* kin, cons
 }
 
 template <typename T> int stage_vec(int nx);
-template <> int stage_vec<float>(int nx) { return nx % 4 == 0 ? 4 : 1; }
+template <> int stage_vec<float>(int nx) { return nx % 2 == 0 ? 2 : 1; }
 template <> int stage_vec<double>(int nx) { return nx % 2 == 0 ? 2 : 1; }
 
 // an upper bound on the blocks launch_stage uses (the scalar path has the most)
@@ -502,14 +498,10 @@ template <typename T> void launch_stage(const StageParams<T>& p0, cudaStream_t s
     if (p.dmi) {
         // DMI runs the general (non-uniform) variant
         if (vec == 1) stage_kernel<T, 1, false, true><<<grid, block, 0, st>>>(p);
-        else if constexpr (sizeof(T) == 4) stage_kernel<T, 4, false, true><<<grid, block, 0, st>>>(p);
         else stage_kernel<T, 2, false, true><<<grid, block, 0, st>>>(p);
     } else if (vec == 1) {
         if (uni) stage_kernel<T, 1, true, false><<<grid, block, 0, st>>>(p);
         else stage_kernel<T, 1, false, false><<<grid, block, 0, st>>>(p);
-    } else if constexpr (sizeof(T) == 4) {
-        if (uni) stage_kernel<T, 4, true, false><<<grid, block, 0, st>>>(p);
-        else stage_kernel<T, 4, false, false><<<grid, block, 0, st>>>(p);
     } else {
         if (uni) stage_kernel<T, 2, true, false><<<grid, block, 0, st>>>(p);
         else stage_kernel<T, 2, false, false><<<grid, block, 0, st>>>(p);

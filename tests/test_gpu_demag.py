@@ -1,9 +1,9 @@
 """GPU parity of the demag field (Sec. 4.4): the five FFT passes of libmm.so
 against the oracle's convolution, element by element, FP64 and FP32, on grids
 that cover one cell, 1-D and 2-D lines, ragged extents that pad beyond 2n,
-every 5-smooth padded length of the mixed-radix passes (100, 200, 400, 800,
-on each axis), several CTA tiles with ragged tails, and the largest padded
-extent (4096)."""
+every mixed-radix padded length r 2^a (r = 3: 96 ... 768, r = 7: 112 ... 896,
+r = 25: 100 ... 800) on at least one axis, several CTA tiles with ragged
+tails, and the largest padded extent (4096)."""
 import numpy as np
 import pytest
 
@@ -27,11 +27,29 @@ GRIDS = [
     ((6, 5, 40), (2e-9, 2e-9, 2e-9)),
     ((2048, 2, 1), (1e-9, 1e-9, 1e-9)),
     ((200, 6, 2), (2e-9, 2e-9, 2e-9)),          # x padded to 400
-    ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 800
-    ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 400
-    ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 100
+    ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 768
+    ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 384
+    ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 96
     ((512, 3, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 1024
     ((1024, 2, 1), (2e-9, 2e-9, 2e-9)),         # x padded to 2048
+    # every mixed-radix length r 2^a (r = 3, 7, 25) on at least one axis
+    ((50, 5, 3), (2e-9, 2e-9, 2e-9)),           # x 100
+    ((3, 100, 2), (2e-9, 2e-9, 2e-9)),          # y 200
+    ((5, 4, 50), (2e-9, 2e-9, 2e-9)),           # z 100
+    ((400, 3, 1), (2e-9, 2e-9, 2e-9)),          # x 800
+    ((56, 6, 3), (2e-9, 2.5e-9, 3e-9)),         # x 112
+    ((4, 112, 2), (2e-9, 2e-9, 2e-9)),          # y 224
+    ((4, 3, 56), (2e-9, 2e-9, 1e-9)),           # z 112
+    ((224, 3, 2), (2e-9, 2e-9, 2e-9)),          # x 448
+    ((448, 2, 1), (2e-9, 2e-9, 2e-9)),          # x 896
+    ((3, 96, 2), (2e-9, 2e-9, 2e-9)),           # y 192
+    ((6, 5, 96), (2e-9, 2e-9, 2e-9)),           # z 192
+    ((3, 3, 112), (2e-9, 2e-9, 2e-9)),          # z 224
+    ((2, 2, 192), (2e-9, 2e-9, 2e-9)),          # z 384
+    ((2, 2, 224), (2e-9, 2e-9, 2e-9)),          # z 448
+    ((2, 1, 384), (2e-9, 2e-9, 2e-9)),          # z 768
+    ((2, 1, 400), (2e-9, 2e-9, 2e-9)),          # z 800
+    ((2, 1, 448), (2e-9, 2e-9, 2e-9)),          # z 896
 ]
 
 
@@ -39,8 +57,11 @@ def test_padded_extents_rule():
     from paper_2302_08843_gb300.binding import padded_extents
     assert padded_extents((1, 2, 3)) == (1, 4, 8)
     assert padded_extents((50, 64, 100)) == (100, 128, 200)
-    assert padded_extents((150, 200, 300)) == (400, 400, 800)
-    assert padded_extents((401, 2048, 33)) == (1024, 4096, 100)
+    assert padded_extents((150, 200, 300)) == (384, 400, 768)
+    assert padded_extents((401, 2048, 33)) == (896, 4096, 96)
+    assert padded_extents((48, 56, 96)) == (96, 112, 192)
+    assert padded_extents((49, 57, 97)) == (100, 128, 200)
+    assert padded_extents((112, 224, 449)) == (224, 448, 1024)
 
 
 def _m(n, seed):
