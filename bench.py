@@ -490,13 +490,63 @@ def layers_measure(torch, hbm_peak, steps=20, warmup=3):
     return out
 
 
+def mixed_measure(torch, hbm_peak, n=(192, 192, 48), steps=20, warmup=3):
+    """The bulk construction on a grid whose padded axes are mixed-radix
+    lengths (192x192x48 -> 384x384x96; powers of two would need 512x512x128,
+    2.4x the points): RK4 in FP32 and FP64 through the classic passes,
+    cell-updates/s per stage (device-timed), and each pass's algorithmic bytes
+    against the HBM roofline from a profiled run of the same steps."""
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import setup_workload
+    w = W.bulk(n=n)
+    stream = torch.cuda.current_stream()
+    out = {"n": list(n), "padded": padded(n)}
+    for prec, rs in (("fp32", 4), ("fp64", 8)):
+        st = steps if prec == "fp32" else max(2, steps // 10)
+        s = setup_workload(w, prec, stream=stream)
+        t = 0.0
+        for _ in range(warmup):
+            t, _ = s.step(w.dt, t, "rk4")
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(st):
+            t, _ = s.step(w.dt, t, "rk4")
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        s.profile_enable(True)
+        for _ in range(st):
+            t, _ = s.step(w.dt, t, "rk4")
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile_enable(False)
+        s.close()
+        kb = kernel_bytes(n, rs, grains=True)
+        tot = sum(v[1] for v in prof.values())
+        kern = {}
+        for name, (cnt, tms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            us = 1e3 * tms / max(cnt, 1)
+            e = {"launches": cnt, "us_per_launch": round(us, 2), "share": round(tms / tot, 4)}
+            if name in kb:
+                e["algorithmic_bytes"] = int(kb[name])
+                e["frac_of_measured_hbm"] = round(kb[name] / (us * 1e-6) / 1e9 / hbm_peak, 4)
+            kern[name] = e
+        out[prec] = {"ms_per_step": round(ms / st, 4), "cell_updates_per_s": w.ncells * 4 * st / (ms / 1e3),
+                     "kernels": kern}
+    torch.cuda.empty_cache()
+    return out
+
+
 def workloads_measure(torch, hbm_peak=6800.0):
     """Time to solution of the paper-shaped configurations beside the bulk one
     (wall time with the device synchronised): plain FP64 (32x32x4, 200 RK4
     steps), the thin film (512x128x1, DP45 with rtol 1e-5 to 1 ns, FP64 and
     FP32 fields), the inverse design (128x128x1, 2000 FP32 RK4 steps and the
-    gradient of the time-averaged output m_y by the checkpointed adjoint) and
-    the non-equidistant multilayer (256x256x8, RK4, layers_measure)."""
+    gradient of the time-averaged output m_y by the checkpointed adjoint), the
+    non-equidistant multilayer (256x256x8, RK4, layers_measure) and the
+    mixed-radix grid (192x192x48, RK4, mixed_measure)."""
     from paper_2302_08843_gb300 import workloads as W
     from paper_2302_08843_gb300.autodiff import rk4_observable
     from paper_2302_08843_gb300.binding import State, setup_workload
@@ -518,6 +568,11 @@ def workloads_measure(torch, hbm_peak=6800.0):
     w = W.thin_film()
     for prec in ("fp64", "fp32"):
         s = setup_workload(w, prec)
+        # untimed warm-up (first launches of the DP45 kernels), then from m0 again
+        t, dt = 0.0, 1e-13
+        for _ in range(3):
+            t, dt = s.step(dt, t, "dp45", w.extra["rtol"])
+        s.set_m(to_soa(w.m0))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         t, dt, steps = 0.0, 1e-13, 0
@@ -539,6 +594,11 @@ def workloads_measure(torch, hbm_peak=6800.0):
     weight[x0:x1, y0:y1, :, 1] = 1.0 / ((x1 - x0) * (y1 - y0))
     weight = torch.from_numpy(to_soa(weight)).float().cuda()
     wt = torch.tensor(to_soa(w.extra["w"]), dtype=torch.float64, device="cuda", requires_grad=True)
+    # untimed warm-up: a 200-step rollout and its gradient (first launches of
+    # the adjoint kernels and of autograd take seconds in a fresh process)
+    rk4_observable(torch.sigmoid(wt) * w.extra["Ms0"], s, m0, weight, w.dt, 200, 100,
+                   dict(A=w.A, alpha=w.alpha)).mean().backward()
+    wt.grad = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     obs = rk4_observable(torch.sigmoid(wt) * w.extra["Ms0"], s, m0, weight, w.dt, w.steps, 100,
@@ -555,6 +615,7 @@ def workloads_measure(torch, hbm_peak=6800.0):
     s.close()
     torch.cuda.empty_cache()
     out["multilayer_256x256x8_rk4"] = layers_measure(torch, hbm_peak)
+    out["mixed_radix_192x192x48_rk4"] = mixed_measure(torch, hbm_peak)
     return out
 
 
@@ -845,6 +906,9 @@ def main():
                          "result)")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the served stream to run (512 = all; 0 = skip)")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="profiling case: only the 192x192x48 mixed-radix grid (the printed line is not a bench "
+                         "result)")
     ap.add_argument("--layers-only", action="store_true",
                     help="profiling case: only the 256x256x8 non-equidistant stack (the printed line is not a "
                          "bench result)")
@@ -853,6 +917,12 @@ def main():
         args.warmup = 3
     if args.layers_only:
         run_layers_only(args)
+    elif args.mixed_only:
+        import torch
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        res = mixed_measure(torch, peaks.get("hbm_gbs", 6800.0), steps=args.steps, warmup=args.warmup)
+        print(json.dumps({"case": "mixed-radix 192x192x48 (profiling case)", "mixed": res}))
     elif args.impl == "reference":
         run_reference(args)
     else:
