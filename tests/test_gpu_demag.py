@@ -50,6 +50,12 @@ GRIDS = [
     ((2, 1, 384), (2e-9, 2e-9, 2e-9)),          # z 768
     ((2, 1, 400), (2e-9, 2e-9, 2e-9)),          # z 800
     ((2, 1, 448), (2e-9, 2e-9, 2e-9)),          # z 896
+    # FP32 TMA z pass on 3 x 2^a lines (also as the 2-D path along y), and
+    # TMA y tiles split into several boxes of uneven rows
+    ((5, 40, 1), (2e-9, 2e-9, 2e-9)),           # y 96, 2-D
+    ((4, 90, 1), (2e-9, 2e-9, 2e-9)),           # y 192, 2-D
+    ((3, 300, 2), (2e-9, 2e-9, 2e-9)),          # y 768
+    ((2, 450, 2), (2e-9, 2e-9, 2e-9)),          # y 1024: forward 2 boxes of 240 rows
 ]
 
 
