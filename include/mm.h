@@ -325,7 +325,7 @@ mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out)
  * this entry point exists for callers that cannot allocate device memory when
  * they need a field -- code capturing a stream into a CUDA graph, where a
  * cudaMalloc would break the capture, frameworks whose allocator owns all
- * device memory, or loops that must not stall on the driver's allocator.
+ * device memory, or loops that must not stall on the CUDA allocator.
  * It runs the same five FFT passes as mm_heff's demag term on caller buffers:
  *   m        device, [3][nz][ny][nx] in the precision's real type;
  *   Ms_cell  device, nx*ny*nz real values, or NULL to use Ms for every cell;

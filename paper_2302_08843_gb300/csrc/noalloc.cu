@@ -7,7 +7,7 @@
 // field, e.g. a caller that is capturing a stream into a CUDA graph (a
 // cudaMalloc would break the capture), a framework whose allocator owns all
 // device memory and forbids side allocations, or a real-time loop that must
-// not stall on the driver's allocator.  Such a caller still owns and passes
+// not stall on the CUDA allocator.  Such a caller still owns and passes
 // every input and output buffer.
 #include <cuda_runtime.h>
 
