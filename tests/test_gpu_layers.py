@@ -1,7 +1,8 @@
 """GPU parity of non-equidistant layers (Sec. 4.4): demag with the lateral
 FFT and dense layer coupling, thickness-weighted exchange links and per-layer
 cell volumes, against the oracle; RK4 trajectories; the full-size stack on
-sampled cells; the reduction to the equidistant grid; refusals."""
+sampled cells; the reduction to the equidistant grid; RKF45 steps and relax
+without precession; refusals."""
 import numpy as np
 import pytest
 
@@ -211,4 +212,51 @@ def test_layers_refusals():
     s.set_layers(None)
     s.set_dmi("interface", 1e-3)
     assert code(lambda: s.set_layers(w.extra["layers"])) == "MM_EINVAL"
+    s.close()
+
+
+def test_layers_rkf45_steps():
+    """RKF45 (the paper's default solver) on the stack: accepted times, step sizes, states."""
+    from oracle.llg import rkf45_step
+    from paper_2302_08843_gb300.workloads import from_soa
+    w, s, prob = _setup((24, 20, 5), "fp64")
+    rtol = 1e-5
+    m, t, dt = w.m0.copy(), 0.0, 1e-14
+    tg, dtg = 0.0, 1e-14
+    for step in range(6):
+        m, t, dt = rkf45_step(prob, m, t, dt, rtol)
+        tg, dtg = s.step(dtg, tg, "rkf45", rtol)
+        assert abs(tg - t) <= 1e-9 * t and abs(dtg - dt) <= 1e-6 * dt, (step, tg, t, dtg, dt)
+    assert rel(from_soa(to_host(s.get_m())), m) < 1e-9
+    s.close()
+
+
+def test_layers_relax_without_precession():
+    """Relax (RKF45, no precession term) of a small three-layer stack: step
+    count, torque, time and state."""
+    from oracle.llg import Problem, relax
+    from paper_2302_08843_gb300.binding import State
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    rng = np.random.default_rng(33)
+    n = (12, 8, 3)
+    hl = [3e-9, 1.5e-9, 4e-9]
+    m0 = rng.normal(size=n + (3,))
+    m0 /= np.linalg.norm(m0, axis=-1, keepdims=True)
+    s = State(n, (3e-9, 3e-9, 1e-9), "fp64")
+    s.set_material(Ms=8e5, A=1.3e-11, alpha=1.0)
+    s.set_layers(hl)
+    s.demag_setup(20)
+    s.set_m(to_soa(m0))
+    s.set_llg_options(relax_method="rkf45", precession=False)
+    steps, tq, t, _ = s.relax(tol=1e-3, max_steps=3000, rtol=1e-5)
+    prob = Problem(n, (3e-9, 3e-9, 1e-9), Ms=8e5, A=1.3e-11, alpha=1.0, p=20, precession=False, layers=hl)
+    mr, steps_r, tq_r, t_r = relax(prob, m0, tol=1e-3, max_steps=3000, method="rkf45")
+    assert steps == steps_r
+    assert tq < 1e-3 and abs(tq - tq_r) < 1e-6 * tq_r
+    # each accepted step sets the next from err^(-1/5), err a difference of two
+    # nearly equal solutions; the layered tensor's FP64 rounding floor is about 3x
+    # the equidistant one (layered_rounding_sensitivity), and over ~1000 controller
+    # updates the time and state agree to ~1e-8 (1e-9 on the equidistant grid)
+    assert abs(t - t_r) <= 1e-7 * t_r
+    assert rel(from_soa(to_host(s.get_m())), mr) < 1e-7
     s.close()
