@@ -321,6 +321,16 @@ mm_status mm_demag_tensor_host(const mm_grid* grid, int p_newell, double* out);
  * doubles (kx fastest), already multiplied by -1/(Px Py Pz). */
 mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out);
 
+/* Host-only helper (no GPU): the layer-pair spectrum mm_demag_setup builds
+ * after mm_set_layers (Sec. 4.4, non-equidistant layers) for a grid whose nz
+ * layers have thicknesses h[0..nz-1] (grid->dz unused), over the padded
+ * lateral grid Px x Py of mm_state_create.  Pairs i <= j only, pair index
+ * q(i, j) = i nz - i (i - 1) / 2 + j - i, as 6 x npair x (Py/2+1) x (Px/2+1)
+ * doubles (kx fastest, npair = nz (nz + 1) / 2), multiplied by -1/(Px Py):
+ * xx, xy, yy, zz are the real spectra, xz and yz the value t of the spectrum
+ * -i t.  out must hold that many.  MM_EINVAL for a bad grid or thickness. */
+mm_status mm_layers_spectrum_host(const mm_grid* grid, const double* h, int p_newell, double* out);
+
 /* Demag field without any memory allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
  * they need a field -- code capturing a stream into a CUDA graph, where a

@@ -28,7 +28,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
            "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent",
-           "mm_set_layers")
+           "mm_set_layers", "mm_layers_spectrum_host")
 
 
 class MMError(RuntimeError):
@@ -100,6 +100,7 @@ def lib():
         "mm_set_dmi": (i, [vp, i, d, vp, i]),
         "mm_fft_extent": (i, [i]),
         "mm_set_layers": (i, [vp, vp, i]),
+        "mm_layers_spectrum_host": (i, [ctypes.POINTER(mm_grid), vp, i, vp]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
     }
@@ -153,6 +154,19 @@ def demag_spectrum_host(n, dx, p=20):
     g = mm_grid(int(n[0]), int(n[1]), int(n[2]), float(dx[0]), float(dx[1]), float(dx[2]))
     out = np.zeros((6, P[2] // 2 + 1, P[1] // 2 + 1, P[0] // 2 + 1))
     check(lib().mm_demag_spectrum_host(ctypes.byref(g), int(p), out.ctypes.data))
+    return out
+
+
+def layers_spectrum_host(n, dx, dy, h, p=20):
+    """mm_layers_spectrum_host: (6, npair, Py/2+1, Px/2+1), pairs i <= j, scaled by -1/(Px Py)."""
+    P = padded_extents((n[0], n[1], 1))
+    nz = int(n[2])
+    g = mm_grid(int(n[0]), int(n[1]), nz, float(dx), float(dy), 1.0)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    if hh.size != nz:
+        raise ValueError("one thickness per layer")
+    out = np.zeros((6, nz * (nz + 1) // 2, P[1] // 2 + 1, P[0] // 2 + 1))
+    check(lib().mm_layers_spectrum_host(ctypes.byref(g), hh.ctypes.data, int(p), out.ctypes.data))
     return out
 
 

@@ -1523,6 +1523,20 @@ mm_status mm_demag_spectrum_host(const mm_grid* grid, int p_newell, double* out)
     return MM_OK;
 }
 
+mm_status mm_layers_spectrum_host(const mm_grid* grid, const double* h, int p_newell, double* out) {
+    if (!grid || !h || !out) return fail(MM_EINVAL, "null argument");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0) || !(grid->dy > 0))
+        return fail(MM_EINVAL, "bad grid");
+    for (int k = 0; k < grid->nz; ++k)
+        if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(MM_EINVAL, "layer %d thickness must be > 0", k);
+    const int Px = fft_extent(grid->nx), Py = fft_extent(grid->ny);
+    if (Px > kMaxFft || Py > kMaxFft) return fail(MM_EINVAL, "padded extent too large");
+    std::vector<double> spec;
+    tensor_layers_spectrum(grid->nx, grid->ny, grid->nz, grid->dx, grid->dy, h, p_newell, Px, Py, Px / 2 + 1, spec);
+    std::memcpy(out, spec.data(), sizeof(double) * spec.size());
+    return MM_OK;
+}
+
 mm_status mm_state_info(const mm_state* s, int out[5]) {
     MM_TRY(check_state(s));
     if (!out) return fail(MM_EINVAL, "null out");

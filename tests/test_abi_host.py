@@ -67,3 +67,41 @@ def test_host_spectrum_matches_oracle_fft(mmlib, n, d, p):
     l1 = np.sum(np.abs(mmlib.demag_tensor_host(n, d, p) - ref_t), axis=(1, 2, 3)) * abs(scale)
     for c in range(6):
         assert np.max(np.abs(ours[c] - ref_oct[c].real)) <= l1[c] + 1e-13 * mag, c
+
+
+@pytest.mark.parametrize("n,h,p", [((8, 4, 3), (1.0e-9, 2.5e-9, 0.7e-9), 20),
+                                   ((16, 8, 2), (3.0e-9, 1.0e-9), 3),
+                                   ((4, 1, 4), (0.6e-9, 1.1e-9, 2.4e-9, 0.8e-9), 20),
+                                   ((1, 4, 2), (2.0e-9, 0.5e-9), 20)])
+def test_host_layers_spectrum_matches_oracle_fft(mmlib, n, h, p):
+    """The library's layer-pair spectrum (pairs i <= j) against numpy.fft of
+    the oracle's layer-pair tensor embedded in the library's padded lateral
+    grid: real components equal the real part, xz and yz store t with
+    spectrum -i t, and every other part vanishes.  The two real-space tensors
+    are independent FP64 evaluations, so the bound is their rounding noise,
+    far below the size of a wrong sign, pair or scale."""
+    from oracle.layers import layered_tensor
+    dx, dy = 2e-9, 2.5e-9
+    nx, ny, nz = n
+    P = mmlib.padded_extents((nx, ny, 1))
+    ours = mmlib.layers_spectrum_host(n, dx, dy, h, p)
+    T = layered_tensor(n, dx, dy, h, p)                    # (6, nz, nz, 2nx-1, 2ny-1)
+    K = np.zeros((6, nz, nz, P[0], P[1]))
+    for X in range(-nx + 1, nx):
+        for Y in range(-ny + 1, ny):
+            K[:, :, :, X % P[0], Y % P[1]] = T[:, :, :, X + nx - 1, Y + ny - 1]
+    Kh = np.fft.fft2(K, axes=(3, 4)) * (-1.0 / (P[0] * P[1]))
+    Kh = Kh[:, :, :, : P[0] // 2 + 1, : P[1] // 2 + 1]
+    mag = np.max(np.abs(Kh))
+    q = 0
+    for i in range(nz):
+        for j in range(i, nz):
+            for c in range(6):
+                ref = np.transpose(Kh[c, i, j])             # [ky][kx]
+                if c in (2, 4):                             # spectrum -i t
+                    assert np.max(np.abs(ref.real)) < 1e-10 * mag
+                    assert np.max(np.abs(ours[c, q] + ref.imag)) < 1e-9 * mag, (c, i, j)
+                else:
+                    assert np.max(np.abs(ref.imag)) < 1e-10 * mag
+                    assert np.max(np.abs(ours[c, q] - ref.real)) < 1e-9 * mag, (c, i, j)
+            q += 1
