@@ -33,7 +33,7 @@ METRIC = "cell-updates/s per RK stage at 256x256x64 (FP32 fields)"
 UNIT = "cell-updates/s"
 WORKLOAD = "bulk 256x256x64 cells of 2 nm, Ms 1e6 A/m, A 1.5e-11 J/m, Ku1 4e5 J/m^3 on 64 Voronoi grains, alpha 0.1, RK4 dt 5e-14 s"
 STAGES_PER_STEP = 4
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, see the design doc
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate: used only if the probe cannot run
 
 
 # ----------------------------------------------------------------- models --
@@ -165,6 +165,38 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------- FP64 peak --
+def fp64_peak_measure(torch, gpu_indices):
+    """FP64 FMA rate of this GPU: the library's probe kernel (8 CTAs of 256
+    threads per SM, every thread 8 independent chains of dependent FMAs),
+    timed with CUDA events on the launching stream after warm-up launches,
+    with the SM clock sampled meanwhile.  Changes no GPU setting."""
+    from paper_2302_08843_gb300.binding import probe_fp64_fma
+    stream = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = 8 * nsm, 4096
+    for _ in range(3):
+        probe_fp64_fma(stream.cuda_stream, sink.data_ptr(), blocks, iters)
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    sampler.start()
+    time.sleep(0.3)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    fl = 0.0
+    a.record(stream)
+    for _ in range(40):
+        fl += probe_fp64_fma(stream.cuda_stream, sink.data_ptr(), blocks, iters)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop(gpu_indices)
+    ms = a.elapsed_time(b)
+    return {"tflops": round(fl / (ms / 1e3) / 1e12, 4), "launches": 40, "ms": round(ms, 3),
+            "kernel": "fp64_fma_probe_kernel (%d CTAs x 256 threads, 8 chains x %d FMAs per thread)" % (blocks, iters),
+            "clocks": clocks}
+
+
 # ---------------------------------------------------------- CPU baseline --
 def _oracle_sample(result_path, n_stages, crop):
     """Time RK stages of the unmodified oracle on the bulk workload (or a crop
@@ -194,7 +226,9 @@ def _oracle_sample(result_path, n_stages, crop):
             kw = {"layers": ws.extra["layers"]}
         sec = stages(ws, 3, **kw)
         small[name] = {"cell_updates_per_s": ws.ncells * 3 / sec, "stages": 3, "seconds": round(sec, 3)}
-    json.dump({"seconds": el, "stages": n_stages, "cells": w.ncells, "n": list(w.n), "small": small},
+    from oracle.demag import FFT_BACKEND, FFT_WORKERS
+    json.dump({"seconds": el, "stages": n_stages, "cells": w.ncells, "n": list(w.n), "small": small,
+               "cpu_count": os.cpu_count(), "fft": FFT_BACKEND, "fft_workers": FFT_WORKERS},
               open(result_path, "w"))
 
 
@@ -217,8 +251,10 @@ def finish_cpu_baseline(p, path, sample_desc):
             os.unlink(path)
         except OSError:
             pass
-    return {"value": r["cells"] * r["stages"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample_desc % r, "small_configs": r.get("small")}
+    return {"value": r["cells"] * r["stages"] / r["seconds"], "unit": UNIT, "cores": r["fft_workers"],
+            "kind": "oracle", "sample": sample_desc % r, "host_cpu_count": r["cpu_count"],
+            "threads": "FFTs: %s; the element-wise NumPy terms: 1 thread" % r["fft"],
+            "small_configs": r.get("small")}
 
 
 # ------------------------------------------------------------------ ours --
@@ -743,13 +779,19 @@ def run_ours(args):
         del s
         torch.cuda.empty_cache()
 
+    fp64_peak = None
+    if not args.nz:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        idx = [int(x) for x in vis.split(",")] if vis and all(x.strip().isdigit() for x in vis.split(",")) \
+            else list(range(ws))
+        fp64_peak = fp64_peak_measure(torch, set(idx[local:local + 1]) if ws > 1 else set(idx[:1]))
     # the oracle process has overlapped the device-timed sections; the served
     # stream and the other configurations are partly host-bound (launch loops,
     # field callbacks), so they run after it has finished
     cpu_res = None
     if cpu is not None:
         cpu_res = finish_cpu_baseline(*cpu, sample_desc="%(stages)d RK stages of the FP64 oracle on the "
-                                      "full 256x256x64 bulk workload (%(seconds).1f s, one host core)")
+                                      "full 256x256x64 bulk workload (%(seconds).1f s; %(fft)s)")
     serving = None
     if args.serve_requests > 0 and not args.nz:
         serving = serve_measure(torch, args.serve_requests, dist, rank, ws)
@@ -811,13 +853,16 @@ def run_ours(args):
     fl = stage_flops(w.n)
     st64 = r64["ms"] / r64["steps"] / STAGES_PER_STEP
     kernels64, dom64 = roofline_info(r64["prof"], 8, "fp64", r64["steps"])
+    if fp64_peak is not None:
+        p64, p64_src = fp64_peak["tflops"], "measured: FP64 FMA probe on this GPU (fp64.peak_probe)"
+    else:
+        p64, p64_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate (probe not run)"
     fp64 = {"value": v64, "unit": UNIT, "ms_per_step": round(r64["ms"] / r64["steps"], 4), "steps": r64["steps"],
             "roofline": {"bound": "alu", "achieved": round(fl / (st64 / 1e3) / 1e12, 4),
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": round(fl / (st64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
-                         "flops_per_stage": int(fl)},
-            "kernels": kernels64, "dominant": dom64}
+                         "peak": p64, "unit": "TFLOP/s",
+                         "frac": round(fl / (st64 / 1e3) / 1e12 / p64, 4),
+                         "peak_source": p64_src, "flops_per_stage": int(fl)},
+            "kernels": kernels64, "dominant": dom64, "peak_probe": fp64_peak}
     el, nbytes, e2e_steps = r32["e2e"]
     e2e = {"value": ws * N * STAGES_PER_STEP * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
@@ -875,12 +920,15 @@ def run_reference(args):
         m = m + 0.5 * w.dt * prob.rhs(m, 0.0)
     el = time.perf_counter() - t0
     value = w.ncells * args.steps / el
-    sample = "one RK stage per step of the FP64 oracle on the %dx%dx%d crop of the bulk workload" % tuple(w.n)
+    from oracle.demag import FFT_BACKEND, FFT_WORKERS
+    sample = ("one RK stage per step of the FP64 oracle on the %dx%dx%d crop of the bulk workload (%s; "
+              "element-wise NumPy terms on 1 thread)" % (tuple(w.n) + (FFT_BACKEND,)))
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": {"workload": WORKLOAD, "sample_grid": list(w.n)},
-                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": FFT_WORKERS, "kind": "oracle",
+                                       "sample": sample, "host_cpu_count": os.cpu_count()},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 

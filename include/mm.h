@@ -22,6 +22,9 @@
  *   acceptance, mm_relax, mm_get_m to host), which synchronise that stream.
  * Errors: every function returns an mm_status; mm_last_error() gives a
  *   thread-local message for the last failure.  Nothing aborts or throws.
+ * Devices: per-device constant tables (FFT twiddles) are uploaded on a
+ *   device's first use and kept for the process; after cudaDeviceReset on a
+ *   device, do not use the library on that device again.
  * Cells with Ms = 0 carry no effective field (the nan_to_num of the
  *   anisotropy listing in Sec. 4.1, applied to every term).
  */
@@ -301,6 +304,17 @@ mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession
  * spins < 1. */
 mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins);
 
+/* Measurement helper (the paper has no counterpart): enqueue on cuda_stream
+ * (NULL = legacy default stream) a kernel of `blocks` CTAs x 256 threads in
+ * which every thread runs 8 independent chains of `iters` dependent FP64
+ * fused multiply-adds, and return in *flops_out the FLOPs it performs
+ * (2 per FMA).  Timed by the caller with CUDA events on that stream, it gives
+ * the FP64 FMA rate the plain-FP64 path is compared with.  sink: device
+ * pointer to one double, never written in practice (it keeps the work
+ * alive).  Changes no GPU setting.  MM_EINVAL for a null pointer,
+ * blocks outside 1..2^20 or iters < 1; MM_ECUDA if the launch fails. */
+mm_status mm_probe_fp64_fma(void* cuda_stream, double* sink, int blocks, int iters, double* flops_out);
+
 /* Host-only helper (no GPU): the padded FFT extent the library uses along an
  * axis of n cells (Sec. 4.4 zero padding, P >= 2n): 1 for n = 1, otherwise the
  * smallest length >= 2n among the powers of two up to 4096 and the lengths
@@ -333,9 +347,9 @@ mm_status mm_layers_spectrum_host(const mm_grid* grid, const double* h, int p_ne
 
 /* Demag field without any memory allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
- * they need a field -- code capturing a stream into a CUDA graph, where a
- * cudaMalloc would break the capture, frameworks whose allocator owns all
- * device memory, or loops that must not stall on the CUDA allocator.
+ * they need a field -- frameworks whose allocator owns all device memory and
+ * forbids side allocations, or loops that must not stall on the CUDA
+ * allocator (cudaMalloc and cudaFree can synchronise the device).
  * It runs the same five FFT passes as mm_heff's demag term on caller buffers:
  *   m        device, [3][nz][ny][nx] in the precision's real type;
  *   Ms_cell  device, nx*ny*nz real values, or NULL to use Ms for every cell;
@@ -349,7 +363,9 @@ mm_status mm_layers_spectrum_host(const mm_grid* grid, const double* h, int p_ne
  * are rejected with MM_EINVAL and a message giving the size needed.  The first
  * call on a device looks up that array's address and uploads the FFT twiddle
  * table (no allocation either); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's data:
+ * capture.  That address is cached per device for the life of the process:
+ * do not call this entry point on a device after cudaDeviceReset there.
+ * All calls share the one array and it keeps the last call's data:
  * calls whose kernels may overlap on the GPU (different streams without
  * ordering, or several host threads) race on it and must be serialised by the
  * caller.  Enqueues on cuda_stream (NULL = legacy default stream) and returns

@@ -11,7 +11,11 @@ Two independent routes are provided:
   (NumPy per target cell, or plain C with one OpenMP thread per target cell);
 * ``demag_fft``: the zero-padded FFT convolution Sec. 4.4 describes ("zero
   padding of the magnetization ... point-wise multiplication in Fourier
-  space"), with numpy.fft over a padding P_a = 2 n_a (P_a = 1 where n_a = 1).
+  space"), over a padding P_a = 2 n_a (P_a = 1 where n_a = 1).
+
+The discrete Fourier transforms are library calls: scipy.fft with one worker
+thread per host core where SciPy is installed, numpy.fft otherwise (the same
+pocketfft algorithm; ``FFT_BACKEND`` says which).
 
 Padding reading: a linear convolution of length n needs P >= 2n - 1.  With
 P = 2n the wrapped offset index n is never used by a valid output; it is set
@@ -24,6 +28,39 @@ import subprocess
 import numpy as np
 
 from .newell import COMPS
+
+try:
+    import scipy.fft as _sfft
+
+    FFT_WORKERS = os.cpu_count() or 1
+    FFT_BACKEND = "scipy.fft, %d workers" % FFT_WORKERS
+
+    def rfftn(a, s, axes):
+        return _sfft.rfftn(a, s=s, axes=axes, workers=FFT_WORKERS)
+
+    def irfftn(a, s, axes):
+        return _sfft.irfftn(a, s=s, axes=axes, workers=FFT_WORKERS)
+
+    def fft2(a, axes):
+        return _sfft.fft2(a, axes=axes, workers=FFT_WORKERS)
+
+    def ifft2(a, axes):
+        return _sfft.ifft2(a, axes=axes, workers=FFT_WORKERS)
+except ImportError:   # numpy.fft: one thread
+    FFT_WORKERS = 1
+    FFT_BACKEND = "numpy.fft, 1 thread"
+
+    def rfftn(a, s, axes):
+        return np.fft.rfftn(a, s=s, axes=axes)
+
+    def irfftn(a, s, axes):
+        return np.fft.irfftn(a, s=s, axes=axes)
+
+    def fft2(a, axes):
+        return np.fft.fft2(a, axes=axes)
+
+    def ifft2(a, axes):
+        return np.fft.ifft2(a, axes=axes)
 
 
 def _full(Nt):
@@ -122,7 +159,7 @@ def tensor_spectrum(Nt, n):
     """rfftn of the six periodic tensor components over the padded grid."""
     P = padded_shape(n)
     K = periodic_kernel(Nt, n)
-    return np.stack([np.fft.rfftn(K[c], s=P, axes=(0, 1, 2)) for c in range(6)])
+    return np.stack([rfftn(K[c], s=P, axes=(0, 1, 2)) for c in range(6)])
 
 
 def demag_fft(Nt, M, Nhat=None):
@@ -131,7 +168,7 @@ def demag_fft(Nt, M, Nhat=None):
     P = padded_shape(n)
     if Nhat is None:
         Nhat = tensor_spectrum(Nt, n)
-    Mhat = [np.fft.rfftn(M[..., b], s=P, axes=(0, 1, 2)) for b in range(3)]
+    Mhat = [rfftn(M[..., b], s=P, axes=(0, 1, 2)) for b in range(3)]
     h = np.empty_like(M)
     for a in range(3):
         acc = np.zeros_like(Mhat[0])
@@ -140,7 +177,7 @@ def demag_fft(Nt, M, Nhat=None):
                 acc = acc + Nhat[c] * Mhat[q]
             elif q == a:
                 acc = acc + Nhat[c] * Mhat[p]
-        h[..., a] = -np.fft.irfftn(acc, s=P, axes=(0, 1, 2))[: n[0], : n[1], : n[2]]
+        h[..., a] = -irfftn(acc, s=P, axes=(0, 1, 2))[: n[0], : n[1], : n[2]]
     return h
 
 
@@ -151,7 +188,7 @@ def rounding_sensitivity(n, dx, p, M, scales=(1e9, 3.7e8)):
     tensor; the largest relative max-norm change of h over the scales is the
     noise floor of a double-precision evaluation (the 27-term sum of Sec. 4.4
     cancels about (r/dx)^6 at offset r).  Used to state the FP64 parity bound
-    as max(1e-10, 2 x this)."""
+    as max(1e-10, this)."""
     from .newell import demag_tensor
     h = demag_fft(demag_tensor(n, dx, p), M)
     sc = np.max(np.abs(h))

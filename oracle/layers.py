@@ -38,6 +38,7 @@ import math
 
 import numpy as np
 
+from .demag import fft2, ifft2
 from .fields import exchange_field
 from .newell import COMP_NAMES, dipole_component, newell_f, newell_g
 
@@ -147,8 +148,8 @@ def layered_demag_fft(T, M):
     for X in range(-nx + 1, nx):
         for Y in range(-ny + 1, ny):
             K[:, :, :, X % Px, Y % Py] = T[:, :, :, X + nx - 1, Y + ny - 1]
-    Kh = np.fft.fft2(K, axes=(3, 4))
-    Mh = np.fft.fft2(np.pad(M, ((0, Px - nx), (0, Py - ny), (0, 0), (0, 0))), axes=(0, 1))
+    Kh = fft2(K, axes=(3, 4))
+    Mh = fft2(np.pad(M, ((0, Px - nx), (0, Py - ny), (0, 0), (0, 0))), axes=(0, 1))
     comp = ((0, 1, 2), (1, 3, 4), (2, 4, 5))
     hh = np.zeros((Px, Py, nz, 3), dtype=complex)
     for i in range(nz):
@@ -156,7 +157,7 @@ def layered_demag_fft(T, M):
             for a in range(3):
                 for b in range(3):
                     hh[:, :, i, a] -= Kh[comp[a][b], i, j] * Mh[:, :, j, b]
-    return np.real(np.fft.ifft2(hh, axes=(0, 1)))[:nx, :ny]
+    return np.real(ifft2(hh, axes=(0, 1)))[:nx, :ny]
 
 
 def thickness_harmonic(Ai, Aj, hi, hj):

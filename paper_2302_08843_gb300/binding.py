@@ -28,7 +28,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
            "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent",
-           "mm_set_layers", "mm_layers_spectrum_host")
+           "mm_set_layers", "mm_layers_spectrum_host", "mm_probe_fp64_fma")
 
 
 class MMError(RuntimeError):
@@ -103,6 +103,7 @@ def lib():
         "mm_layers_spectrum_host": (i, [ctypes.POINTER(mm_grid), vp, i, vp]),
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
+        "mm_probe_fp64_fma": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -139,6 +140,15 @@ def demag_tensor_host(n, dx, p=20):
     out = np.zeros((6, 2 * n[0] - 1, 2 * n[1] - 1, 2 * n[2] - 1))
     check(lib().mm_demag_tensor_host(ctypes.byref(g), int(p), out.ctypes.data))
     return out
+
+
+def probe_fp64_fma(stream, sink, blocks, iters):
+    """mm_probe_fp64_fma: enqueue the FP64 FMA rate probe on a CUDA stream
+    handle; returns the FLOPs it performs (the caller times it)."""
+    fl = ctypes.c_double(0.0)
+    check(lib().mm_probe_fp64_fma(ctypes.c_void_p(stream), ctypes.c_void_p(sink), int(blocks), int(iters),
+                                  ctypes.byref(fl)))
+    return fl.value
 
 
 def padded_extents(n):

@@ -74,6 +74,8 @@ void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool ne
 
 // diagnostic: one CTA whose bounded wait on a never-completed mbarrier runs out
 void launch_diag_wait(int* err, unsigned spins, cudaStream_t st);
+// FP64 FMA rate probe (blocks x 256 threads, iters FMAs per chain); returns the FLOPs it enqueued
+double launch_fp64_fma_probe(double* sink, int blocks, int iters, cudaStream_t st);
 
 template <typename T> struct AdjParams;
 template <typename T> void launch_adj_prep(const AdjParams<T>& p, cudaStream_t st);

@@ -29,3 +29,34 @@ void launch_diag_wait(int* err, unsigned spins, cudaStream_t st) {
 }
 
 }  // namespace mm
+
+// ------------------------------------------------------------------------
+// FP64 FMA rate probe: every thread runs kFmaChains independent chains of
+// dependent fused multiply-adds x <- x a + b (|a| < 1, so the values stay
+// bounded), enough chains per warp that the FP64 pipe, not the dependency
+// latency, sets the rate.  The sum of the chains is written only if it equals
+// an impossible value, so the work is kept but nothing is stored.
+namespace mm {
+
+constexpr int kFmaChains = 8;
+
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(double* sink, int iters, double a, double b) {
+    double x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = 1e-3 * (threadIdx.x + c) + 1e-7 * blockIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    if (s == -1.2345e300) sink[0] = s;
+}
+
+double launch_fp64_fma_probe(double* sink, int blocks, int iters, cudaStream_t st) {
+    fp64_fma_probe_kernel<<<blocks, 256, 0, st>>>(sink, iters, 0.999999, 1e-6);
+    return 2.0 * kFmaChains * (double)iters * 256.0 * (double)blocks;
+}
+
+}  // namespace mm

@@ -1246,6 +1246,16 @@ mm_status mm_selftest_wait_timeout(mm_state* s, unsigned spins) {
     return MM_OK;
 }
 
+mm_status mm_probe_fp64_fma(void* cuda_stream, double* sink, int blocks, int iters, double* flops_out) {
+    if (!sink || !flops_out) return fail(MM_EINVAL, "null argument");
+    if (blocks < 1 || blocks > (1 << 20) || iters < 1) return fail(MM_EINVAL, "blocks must be 1..2^20, iters >= 1");
+    cudaGetLastError();
+    *flops_out = launch_fp64_fma_probe(sink, blocks, iters, (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(MM_ECUDA, "FP64 probe launch: %s", cudaGetErrorString(e));
+    return MM_OK;
+}
+
 mm_status mm_set_layers(mm_state* s, const double* h, int nz) {
     MM_TRY(check_state(s));
     if (!h) {

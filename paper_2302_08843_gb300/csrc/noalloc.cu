@@ -4,11 +4,10 @@
 // allocation.
 //
 // Who needs it: code that may not call cudaMalloc at the moment it wants a
-// field, e.g. a caller that is capturing a stream into a CUDA graph (a
-// cudaMalloc would break the capture), a framework whose allocator owns all
-// device memory and forbids side allocations, or a real-time loop that must
-// not stall on the CUDA allocator.  Such a caller still owns and passes
-// every input and output buffer.
+// field, e.g. a framework whose allocator owns all device memory and forbids
+// side allocations, or a real-time loop that must not stall on the CUDA
+// allocator (cudaMalloc and cudaFree can synchronise the device).  Such a
+// caller still owns and passes every input and output buffer.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -25,7 +24,9 @@ constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_mu;
-void* g_scratch_ptr[128] = {nullptr};   // device address of g_noalloc_scratch per device
+// device address of g_noalloc_scratch per device, looked up on the first call
+// on that device and kept for the process (a cudaDeviceReset invalidates it)
+void* g_scratch_ptr[128] = {nullptr};
 thread_local char g_msg[256];
 
 mm_status err(mm_status st, const char* what) {

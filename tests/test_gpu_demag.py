@@ -94,7 +94,7 @@ def test_demag_matches_oracle(n, d, precision):
     ref = demag_fft(demag_tensor(n, d, 20), M)
     err = rel(h, ref)
     if precision == "fp64":
-        tol = max(1e-10, 2.0 * rounding_sensitivity(n, d, 20, M))
+        tol = max(1e-10, rounding_sensitivity(n, d, 20, M))
     else:
         tol = FP32_TOL
     assert err < tol, (err, tol)

@@ -27,7 +27,7 @@ def _tol(precision, w):
     from oracle.demag import magnetization, rounding_sensitivity
     if precision == "fp32":
         return FP32_TOL
-    return max(1e-10, 2.0 * rounding_sensitivity(w.n, w.dx, 20, magnetization(w.m0, w.Ms)))
+    return max(1e-10, rounding_sensitivity(w.n, w.dx, 20, magnetization(w.m0, w.Ms)))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -37,7 +37,7 @@ def test_heff_and_energies_match_oracle(name, precision):
     Eref = prob.energies(w.m0, t)
     tq_ref = prob.max_torque(w.m0, ref)
     if precision == "fp64":
-        tol = max(1e-10, 2.0 * rounding_sensitivity(w.n, w.dx, 20, magnetization(w.m0, w.Ms)))
+        tol = max(1e-10, rounding_sensitivity(w.n, w.dx, 20, magnetization(w.m0, w.Ms)))
     else:
         tol = FP32_TOL
     assert rel(h, ref) < tol

@@ -40,7 +40,7 @@ def _tol(precision, w):
     if precision == "fp32":
         return FP32_TOL
     M = w.m0 * np.asarray(w.Ms)[..., None]
-    return max(1e-10, 2.0 * layered_rounding_sensitivity(w.n, w.dx[0], w.dx[1], w.extra["layers"], 20, M))
+    return max(1e-10, layered_rounding_sensitivity(w.n, w.dx[0], w.dx[1], w.extra["layers"], 20, M))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -140,6 +140,44 @@ def test_dmi_average():
     assert dmi_average(-1e-3, 4e-3) == v and dmi_average(-4e-3, 1e-3) == -v
 
 
+def test_dmi_average_opposite_signs_properties():
+    """The opposite-sign branch of Eq. D_avg is garbled in print; its reading
+    is pinned by properties any sensible link average has, each of which a
+    dropped square root, a lost factor 1/2 or a flipped sign breaks:
+    symmetry, oddness, degree-1 homogeneity, continuity with the equal-sign
+    branch where one strength vanishes, sign of D_i + D_j, a magnitude between
+    the geometric sqrt(|D_i D_j|) and arithmetic |D_i + D_j| / 2 means (hence
+    at most max(|D_i|, |D_j|)), and zero for equal and opposite strengths."""
+    rng = np.random.default_rng(7)
+    Di = rng.uniform(1e-4, 5e-3, 400)
+    Dj = -rng.uniform(1e-4, 5e-3, 400)
+    v = dmi_average(Di, Dj)
+    assert np.array_equal(v, dmi_average(Dj, Di))                          # symmetric
+    assert np.array_equal(dmi_average(-Di, -Dj), -v)                       # odd
+    for lam in (0.5, 4.0):                                                 # homogeneous of degree 1
+        assert np.array_equal(dmi_average(lam * Di, lam * Dj), lam * v)     # (exact for powers of two)
+    for lam in (3.0, 1e3):
+        assert np.allclose(dmi_average(lam * Di, lam * Dj), lam * v, rtol=1e-9, atol=0)
+    assert np.array_equal(np.sign(v), np.sign(Di + Dj))                    # sign of the sum
+    gm = np.sqrt(-Di * Dj)
+    am = np.abs(Di + Dj) / 2
+    tiny = 1e-12 * np.maximum(gm, am)
+    assert np.all(np.abs(v) >= np.minimum(gm, am) - tiny)                 # between the two means
+    assert np.all(np.abs(v) <= np.maximum(gm, am) + tiny)
+    assert np.all(np.abs(v) <= np.maximum(np.abs(Di), np.abs(Dj)))
+    # continuity through D_j = 0 from both sides (the equal-sign branch gives 0 there)
+    # (from the opposite side it vanishes like |D_j|^(1/4))
+    for d in (3e-3, -2e-3):
+        sg = np.sign(d)
+        opposite = [abs(dmi_average(d, -sg * e)) for e in (1e-6, 1e-12, 1e-30)]
+        same = [abs(dmi_average(d, sg * e)) for e in (1e-6, 1e-9, 1e-12)]
+        assert opposite[0] > opposite[1] > opposite[2] and opposite[2] < 1e-6 * abs(d)
+        assert same[0] > same[1] > same[2] and same[2] < 1e-8 * abs(d)
+        assert dmi_average(d, 0.0) == 0.0
+    # equal magnitudes of opposite sign cancel
+    assert np.all(dmi_average(Di, -Di) == 0.0)
+
+
 @pytest.mark.parametrize("kind", ["interface", "bulk", "d2d"])
 def test_dmi_uniform_m_has_no_interior_field(kind):
     n = (6, 5, 4)

@@ -1,10 +1,15 @@
 """mm_demag_noalloc: the demag field for callers that cannot allocate device
-memory when they need a field (for example while capturing a stream into a
-CUDA graph, or inside a framework whose allocator owns all device memory).
-Its spectra scratch is a fixed array inside the library, so these tests call
-it twice in a row -- the second call finds the first call's data in that
-array -- and compare each result with the demag field that mm_heff computes
-with its own allocated buffers.  Kept in a file that pytest collects last."""
+memory at the moment they need a field (a framework whose allocator owns all
+device memory, or a loop that must not stall on the CUDA allocator).  Its
+spectrum scratch is a fixed array inside the library, so each case calls it
+twice in a row -- the second call finds the first call's data in that array
+-- and compares every result with the oracle's FFT convolution (FP64 bound
+max(1e-10, the oracle's own rounding floor), FP32 1e-5) and with the demag
+field that mm_heff computes with its own allocated buffers.  The shapes reach
+the three layouts of the scratch: a 3-D grid, a 2-D grid (nz = 1, where the
+tensor multiply runs along y and only the x-spectrum is used), a grid with
+ny = 1 (the y-spectrum aliases the x-spectrum) and mixed-radix padded
+extents.  Kept in a file that pytest collects last."""
 import ctypes
 
 import numpy as np
@@ -12,21 +17,31 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
+SHAPES = [
+    ((24, 20, 6), (2.5e-9, 2.5e-9, 3e-9)),
+    ((50, 48, 1), (2e-9, 2e-9, 2e-9)),       # 2-D: padded 100 x 96 x 1
+    ((40, 1, 4), (2e-9, 3e-9, 2e-9)),        # ny = 1
+    ((48, 96, 6), (2e-9, 2e-9, 2.5e-9)),     # padded 96 x 192 x 16
+]
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
 
 def _rel(a, b):
-    a = a.detach().double().cpu().numpy()
-    b = b.detach().double().cpu().numpy()
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("per_cell_ms", [True, False])
-def test_noalloc_matches_heff_on_two_calls(precision, per_cell_ms):
+@pytest.mark.parametrize("n,d", SHAPES)
+def test_noalloc_matches_oracle_and_heff_on_two_calls(n, d, precision, per_cell_ms):
     import torch
+    from oracle.demag import demag_fft, magnetization, rounding_sensitivity
+    from oracle.newell import demag_tensor
     from paper_2302_08843_gb300 import binding as B
-    from paper_2302_08843_gb300.workloads import to_soa
-    n = (24, 20, 6)
-    d = (2.5e-9, 2.5e-9, 3e-9)
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
     dtype = torch.float64 if precision == "fp64" else torch.float32
     prec = B.MM_FP64 if precision == "fp64" else B.MM_FP32_FIELDS
     rng = np.random.default_rng(21)
@@ -40,7 +55,7 @@ def test_noalloc_matches_heff_on_two_calls(precision, per_cell_ms):
     s.demag_setup(20)
     g = B.mm_grid(n[0], n[1], n[2], d[0], d[1], d[2])
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    tol = 1e-10 if precision == "fp64" else 1e-5
+    Nt = demag_tensor(n, d, 20)
     for seed in (1, 2):
         m = np.random.default_rng(seed).normal(size=n + (3,))
         m /= np.linalg.norm(m, axis=-1, keepdims=True)
@@ -49,10 +64,15 @@ def test_noalloc_matches_heff_on_two_calls(precision, per_cell_ms):
         B.check(B.lib().mm_demag_noalloc(ctypes.byref(g), prec, mt.data_ptr(),
                                          None if Ms_dev is None else Ms_dev.data_ptr(), Ms0, spec.data_ptr(),
                                          h.data_ptr(), stream))
-        ref = s.heff(m=mt)
+        ref_lib = s.heff(m=mt)
         torch.cuda.synchronize()
         assert bool(torch.isfinite(h).all())
-        assert _rel(h, ref) < tol
+        M = magnetization(m, Ms if per_cell_ms else Ms0)
+        ref = demag_fft(Nt, M)
+        tol = max(1e-10, rounding_sensitivity(n, d, 20, M)) if precision == "fp64" else 1e-5
+        hg = from_soa(_np(h))
+        assert _rel(hg, ref) < tol, (seed, _rel(hg, ref), tol)
+        assert _rel(_np(h), _np(ref_lib)) < tol
     s.close()
 
 
