@@ -165,6 +165,44 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class UtilSampler:
+    """nvidia-smi utilization.gpu (the share of each sample period in which a
+    kernel was running) sampled every 200 ms while the served stream runs."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,utilization.gpu",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, gpu_indices):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        vals = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == 2 and parts[0].isdigit() and parts[1].isdigit() and int(parts[0]) in gpu_indices:
+                    vals.append(float(parts[1]))
+        os.unlink(self.f.name)
+        if not vals:
+            return None
+        return {"mean": round(statistics.mean(vals) / 100.0, 4), "median": round(statistics.median(vals) / 100.0, 4),
+                "samples": len(vals)}
+
+
 # ---------------------------------------------------------- FP64 peak --
 def fp64_peak_measure(torch, gpu_indices):
     """FP64 FMA rate of this GPU: the library's probe kernel (8 CTAs of 256
@@ -310,7 +348,7 @@ def traffic_for(kernel, precision):
 
 # the files that define the timed FP32 stage kernels (device code and the
 # launch configuration); a change to any of them invalidates stored counters
-KERNEL_SOURCES = ("demag_passes.cu", "fft_engine.cuh", "common.cuh", "tma.cuh", "demag.h")
+KERNEL_SOURCES = ("demag_passes.cu", "fft_engine.cuh", "fft_pair.cuh", "common.cuh", "tma.cuh", "demag.h")
 
 
 def source_hash():
@@ -669,7 +707,13 @@ def serve_measure(torch, n_requests, dist=None, rank=0, ws=1):
     stream = W.serving_stream()
     reqs = stream[:n_requests]
     srv = Server(precision="fp32", hbm_cap=40e9)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    idx = [int(x) for x in vis.split(",")] if vis and all(x.strip().isdigit() for x in vis.split(",")) \
+        else list(range(ws))
+    util = UtilSampler()
+    util.start()
     res, elapsed = serve_replicas(torch, dist, rank, ws, reqs, srv)
+    busy = util.stop(set(idx[rank:rank + 1]) if ws > 1 else set(idx[:1]))
     launches, peak = srv.launches, srv.peak_used
     srv.close()
     torch.cuda.empty_cache()
@@ -677,6 +721,20 @@ def serve_measure(torch, n_requests, dist=None, rank=0, ws=1):
         return None
     summ = latency_summary(res, elapsed)
     cell_steps = sum(w.ncells * r["steps"] for (_, w), r in zip(reqs, res))
+    by_shape = {}
+    for (_, w), r in zip(reqs, res):
+        e = by_shape.setdefault("%dx%dx%d" % tuple(w.n), {"requests": 0, "steps": 0, "hit_max_steps": 0,
+                                                          "latency_s": []})
+        e["requests"] += 1
+        e["steps"] += r["steps"]
+        e["hit_max_steps"] += int(r["status"] == 3)
+        e["latency_s"].append(r["latency"])
+    for e in by_shape.values():
+        lat = e.pop("latency_s")
+        e["mean_steps"] = round(e.pop("steps") / e["requests"], 1)
+        e["p50_s"] = round(float(np.percentile(lat, 50)), 3)
+    summ["by_shape"] = by_shape
+    summ["device_busy"] = busy
     summ.update({"elapsed_s": round(elapsed, 3), "graph_launches_rank0": launches,
                  "cell_steps_per_s": cell_steps / elapsed, "peak_footprint_bytes_rank0": int(peak),
                  "replicas": ws,

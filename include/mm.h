@@ -156,6 +156,17 @@ mm_status mm_demag_disable(mm_state* s);
 mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[5], double t,
                   double* torque_out);
 
+/* Right-hand side of the LLG equation (Eq. llg) at time t for m (device
+ * pointer in the state's layout and type, or NULL for the state's m):
+ * k = -gamma/(1+alpha^2) [m x h + alpha m x (m x h)] with h the field of
+ * mm_heff (without the precession term if mm_set_llg_options switched it
+ * off), written to k_out (device, [3][nz][ny][nx] real).  For an FP32 state
+ * whose RK4 steps run the fused stage kernel (uniform material) this takes
+ * the same kernels, so k is the stage derivative those steps use.  The state's
+ * m and its integrator history are left unchanged; enqueue only.  Cells with
+ * Ms = 0 get k = 0.  MM_EINVAL for a null k_out, MM_ENOTSETUP as mm_heff. */
+mm_status mm_llg_rhs(mm_state* s, const void* m, void* k_out, double t);
+
 /* Advance the state by one step of the LLG equation (Eq. llg).
  * MM_RK4: one classic RK4 step of size *dt_inout from *t_inout (four field
  *   evaluations; enqueue only, no synchronisation).

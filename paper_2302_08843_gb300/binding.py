@@ -28,7 +28,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
            "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent",
-           "mm_set_layers", "mm_layers_spectrum_host", "mm_probe_fp64_fma")
+           "mm_set_layers", "mm_layers_spectrum_host", "mm_probe_fp64_fma", "mm_llg_rhs")
 
 
 class MMError(RuntimeError):
@@ -104,6 +104,7 @@ def lib():
         "mm_batch_end": (i, [vp, vp, vp, vp]),
         "mm_batch_get_m": (i, [vp, i, vp, i]),
         "mm_probe_fp64_fma": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
+        "mm_llg_rhs": (i, [vp, vp, vp, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -309,6 +310,16 @@ class State:
         if torque:
             out.append(tq.value)
         return out[0] if len(out) == 1 else tuple(out)
+
+    def llg_rhs(self, m=None, t=0.0, k_out=None):
+        """mm_llg_rhs: dm/dt of Eq. llg at m (default: the state's m)."""
+        import torch
+        if m is not None:
+            m = self._as_field(m)
+        if k_out is None:
+            k_out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        check(lib().mm_llg_rhs(self.h, None if m is None else m.data_ptr(), k_out.data_ptr(), float(t)))
+        return k_out
 
     def selftest_wait_timeout(self, spins=1 << 16):
         """mm_selftest_wait_timeout: a device wait that runs out on this state's stream."""

@@ -38,7 +38,7 @@ struct FftLine {
     static __device__ __forceinline__ int in_index(int j, int r) { return j + r * TPL; }
     static __host__ __device__ constexpr bool in_live(int r) { return !ZIN || L == 1 || r < NR / 2; }
 
-    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j) {
+    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j, const C* = nullptr) {
         if constexpr (L == 1) {
             return;
         } else if constexpr (L == 2) {
@@ -129,7 +129,7 @@ struct FftLine {
 // (j + r TPL) / 2 and one shared-memory exchange is saved.  Twiddles of a
 // radix-16 pass come from four table loads (w, w^2, w^4, w^8); the other
 // powers are at most three products away.
-template <typename T, int L, int DIR, bool ZIN>
+template <typename T, int L, int DIR, bool ZIN, int SKW = 0>
 struct FftLine16 {
     using C = typename Cplx<T>::type;
     static_assert(L >= 16, "FftLine16 needs L >= 16");
@@ -139,6 +139,10 @@ struct FftLine16 {
     static constexpr int R0 = (K % 4) ? (1 << (K % 4)) : 16;
     static constexpr int NPASS = (K % 4) ? (K / 4 + 1) : (K / 4);
     static constexpr bool FOLD2 = ZIN && R0 == 2;
+
+    // shared-memory place of element e: e LS, plus SKW more every 32 elements
+    // (a skew that spreads the strided exchange writes over the banks)
+    static __device__ __forceinline__ int at(int e, int LS) { return e * LS + (SKW ? (e >> 5) * SKW : 0); }
 
     static __device__ __forceinline__ int in_index(int j, int r) { return FOLD2 ? ((j + r * TPL) >> 1) : (j + r * TPL); }
     static __host__ __device__ constexpr bool in_live(int r) { return FOLD2 || !ZIN || r < 8; }
@@ -157,7 +161,10 @@ struct FftLine16 {
         v[15] = cmul(v[15], cmul(w7, w8));
     }
 
-    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j) {
+    // twk (optional, for plans with one radix-16 pass): the 16 forward twiddles
+    // W_L^(k q L / (16 R0)), q = 0..15, of this thread's butterfly k = j mod R0,
+    // read instead of derived (conjugated for the inverse)
+    static __device__ __forceinline__ void run(C* v, C* s, int LS, int j, const C* twk = nullptr) {
         if constexpr (NPASS == 1) {
             dft16<DIR, ZIN>(v);
             return;
@@ -168,7 +175,7 @@ struct FftLine16 {
                     dft16<DIR, ZIN>(v);
                     __syncthreads();
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) s[(16 * j + q) * LS] = v[q];
+                    for (int q = 0; q < 16; ++q) s[at(16 * j + q, LS)] = v[q];
                 } else if constexpr (R0 == 8) {
                     __syncthreads();
 #pragma unroll
@@ -179,7 +186,7 @@ struct FftLine16 {
                         if (ZIN) dft8_half<DIR>(a); else dft8<DIR>(a);
                         const int b = j + rr * TPL;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) s[(8 * b + q) * LS] = a[q];
+                        for (int q = 0; q < 8; ++q) s[at(8 * b + q, LS)] = a[q];
                     }
                 } else if constexpr (R0 == 4) {
                     __syncthreads();
@@ -198,10 +205,10 @@ struct FftLine16 {
                             dft4<DIR>(a0, a1, a2, a3);
                         }
                         const int b = j + rr * TPL;
-                        s[(4 * b + 0) * LS] = a0;
-                        s[(4 * b + 1) * LS] = a1;
-                        s[(4 * b + 2) * LS] = a2;
-                        s[(4 * b + 3) * LS] = a3;
+                        s[at(4 * b + 0, LS)] = a0;
+                        s[at(4 * b + 1, LS)] = a1;
+                        s[at(4 * b + 2, LS)] = a2;
+                        s[at(4 * b + 3, LS)] = a3;
                     }
                 } else {  // R0 == 2, not zero-padded
                     __syncthreads();
@@ -210,8 +217,8 @@ struct FftLine16 {
                         C a0 = v[rr], a1 = v[rr + 8];
                         dft2<DIR>(a0, a1);
                         const int b = j + rr * TPL;
-                        s[(2 * b + 0) * LS] = a0;
-                        s[(2 * b + 1) * LS] = a1;
+                        s[at(2 * b + 0, LS)] = a0;
+                        s[at(2 * b + 1, LS)] = a1;
                     }
                 }
             }
@@ -222,16 +229,25 @@ struct FftLine16 {
                 if (!(FOLD2 && p == 1)) {
                     __syncthreads();
 #pragma unroll
-                    for (int r = 0; r < 16; ++r) v[r] = s[(j + r * TPL) * LS];
+                    for (int r = 0; r < 16; ++r) v[r] = s[at(j + r * TPL, LS)];
                 }
                 const int k = j & (Ns - 1);
-                twiddle16(v, k * (L / (Ns * 16)));
+                if (NPASS == 2 && twk) {
+#pragma unroll
+                    for (int r = 1; r < 16; ++r) {
+                        C w = twk[r];
+                        if (DIR > 0) w.y = -w.y;
+                        v[r] = cmul(v[r], w);
+                    }
+                } else {
+                    twiddle16(v, k * (L / (Ns * 16)));
+                }
                 dft16<DIR, false>(v);
                 if (p < NPASS - 1) {
                     __syncthreads();
                     const int idxD = (j / Ns) * Ns * 16 + k;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) s[(idxD + q * Ns) * LS] = v[q];
+                    for (int q = 0; q < 16; ++q) s[at(idxD + q * Ns, LS)] = v[q];
                 }
             }
         }

@@ -373,6 +373,43 @@ mm_status heff_impl(mm_state* s, const void* m, void* h_out, double* E_out, doub
     return MM_OK;
 }
 
+// k = f(m, t) (Eq. llg with the field of Sec. 4) into k_out.  FP32 states whose
+// RK4 steps take the fused kernel take it here too (x-forward, y/z/y passes,
+// fused x-inverse + local terms + LLG with the stage derivative as its
+// accumulator output), so the derivative is the one those steps use.
+template <typename T> mm_status rhs_impl(mm_state* s, const void* m, void* k_out, double t) {
+    MM_TRY(ready_for_fields(s));
+    if (!m && !s->have_m) return fail(MM_ENOTSETUP, "no magnetisation: call mm_set_m or pass m");
+    const void* mm_ = m ? m : s->m;
+    if constexpr (sizeof(T) == 4) {
+        StageParams<float> p;
+        fill_common<float>(s, p, mm_, t);
+        if (s->use_fused && !s->demag_off && s->demag_ready && fused_stage_supported(s->d, p)) {
+            demag_front<float>(s->d, (const float*)mm_, (const float*)s->Ms_cell, (float)s->Ms, true,
+                               (float2*)s->S1, (float2*)s->S2, (const float*)s->tens, s->st, &s->timer);
+            MM_LAUNCHED();
+            p.hd = nullptr;
+            p.dt = 0.0;
+            p.next = (float*)s->mB;       // a stage buffer, free between steps
+            p.acc_in = nullptr;
+            p.acc_out = (float*)k_out;
+            p.acc_b = 1.0;
+            p.ck = 0.0;
+            stage_prepare(p);
+            if (!fused_stage(s->d, (float2*)s->S1, p, s->st, &s->timer))
+                return fail(MM_ECUDA, "fused stage kernel could not be launched for this grid");
+            MM_LAUNCHED();
+            s->s1_fresh = false;
+            return MM_OK;
+        }
+    }
+    MM_TRY(run_demag<T>(s, mm_));
+    StageParams<T> p;
+    fill_common<T>(s, p, mm_, t);
+    p.k_out = (T*)k_out;
+    return run_stage<T>(s, p, false);
+}
+
 const double kRK4_C[4] = {0.0, 0.5, 0.5, 1.0};
 
 // RK4 through the fused x-inverse + stage + x-forward kernel (FP32, uniform material)
@@ -1129,6 +1166,13 @@ mm_status mm_heff(mm_state* s, const void* m, void* h_out, double E_out[4], doub
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? heff_impl<double>(s, m, h_out, E_out, t, torque_out)
                               : heff_impl<float>(s, m, h_out, E_out, t, torque_out);
+}
+
+mm_status mm_llg_rhs(mm_state* s, const void* m, void* k_out, double t) {
+    MM_TRY(check_state(s));
+    if (!k_out) return fail(MM_EINVAL, "null k_out");
+    MM_TRY(set_device(s));
+    return s->prec == MM_FP64 ? rhs_impl<double>(s, m, k_out, t) : rhs_impl<float>(s, m, k_out, t);
 }
 
 mm_status mm_llg_step(mm_state* s, mm_method method, double* dt_inout, double rtol, double* t_inout) {
