@@ -4,10 +4,11 @@ Sec. 5.2 obtains gradients with PyTorch's autograd; this module writes the
 same derivative out by hand for the LLG right-hand side (Eq. llg) and the
 classic RK4 step with renormalisation, in float64.
 
-For f(m) = -g' [m x h + a m x (m x h)], h = H m + h_ext (H linear: demag,
-exchange, anisotropy), g' = gamma / (1 + a^2), and a cotangent u of f:
+For f(m) = -g' [p m x h + a m x (m x h)], h = H m + h_ext (H linear: demag,
+exchange, anisotropy, DMI), g' = gamma / (1 + a^2), p = 1 with the
+precession term and 0 without it (Sec. 3), and a cotangent u of f:
 
-    v = u + a (u x m),   w = v x m,   G = m x h
+    v = p u + a (u x m),   w = v x m,   G = m x h
     (df/dm)^T u  = -g' [ h x v + a G x u + H^T w ]
     (df/dMs)^T u = -g' (dh/dMs)^T w
 
@@ -15,6 +16,11 @@ with, per cell j (positive-trace N, M = Ms m):
     demag      H^T w = Ms * (-N * w),   d<w,h_dem>/dMs_j = m_j . (-N * w)_j
     exchange   H^T w = Ms * h_ex(w / Ms) (the operator is D L with L symmetric),
                d<w,h_ex>/dMs_j = -w_j . h_ex_j / Ms_j
+    DMI        the same form: h_dmi = diag(2/(mu0 Ms)) Q m with Q symmetric
+               (a link i, i+k adds c (e_k x m_{i+k}) to cell i and c (e_{-k} x m_i)
+               = -c (e_k x m_i) to cell i+k, and u.(e x m') - u'.(e x m) is
+               symmetric under (u, u') <-> (m, m')), so H^T w = Ms * h_dmi(w / Ms),
+               d<w,h_dmi>/dMs_j = -w_j . h_dmi_j / Ms_j
     anisotropy H^T w = h_u(w) (symmetric per cell), d<w,h_u>/dMs_j = -w_j . h_u_j / Ms_j
     Zeeman     no m or Ms dependence.
 
@@ -27,7 +33,7 @@ import numpy as np
 
 from .constants import GAMMA
 from .demag import demag_fft
-from .fields import anisotropy_field, exchange_field
+from .fields import anisotropy_field, dmi_field, exchange_field
 from .llg import RK4_B, RK4_C, llg_rhs, normalize
 
 
@@ -42,18 +48,21 @@ def _ms(prob):
 
 def rhs_vjp(prob, m, t, u):
     """Returns ((df/dm)^T u, (df/dMs)^T u) at (m, t); the second is (nx, ny, nz).
-    Written for the LLG with precession and without DMI."""
-    if not getattr(prob, "precession", True) or np.any(np.asarray(getattr(prob, "D", 0.0)) != 0):
-        raise ValueError("rhs_vjp covers the LLG with precession and no DMI")
+    Covers the LLG with and without the precession term and DMI of any kind
+    (equidistant grids; non-equidistant layers are not covered)."""
+    if getattr(prob, "layers", None) is not None:
+        raise ValueError("rhs_vjp covers equidistant grids")
     alpha, gp = _gp(prob)
     Ms = _ms(prob)
+    pc = 1.0 if getattr(prob, "precession", True) else 0.0
     h = prob.heff(m, t)
     hex_ = exchange_field(m, prob.Ms, prob.A, prob.dx)
     hu = anisotropy_field(m, prob.Ms, prob.Ku1, prob.ku_axis)
+    hd = dmi_field(m, prob.Ms, prob.D, prob.dx, prob.dmi)
     a = alpha[..., None]
     ok = Ms != 0
     # a cell with Ms = 0 has f = 0 identically: its cotangent reaches nothing
-    v = u + a * np.cross(u, m)
+    v = pc * u + a * np.cross(u, m)
     w = np.cross(v, m) * ok[..., None]
     G = np.cross(m, h)
     inv = np.zeros(prob.n)
@@ -61,9 +70,10 @@ def rhs_vjp(prob, m, t, u):
     hw = demag_fft(prob.Nt, w, prob.Nhat) if prob.demag else np.zeros_like(m)   # -N * w
     q = w * inv[..., None]
     HTw = Ms[..., None] * hw + Ms[..., None] * exchange_field(q, prob.Ms, prob.A, prob.dx) \
+        + Ms[..., None] * dmi_field(q, prob.Ms, prob.D, prob.dx, prob.dmi) \
         + anisotropy_field(w, prob.Ms, prob.Ku1, prob.ku_axis)
     lam = -gp[..., None] * (np.cross(h, v) + a * np.cross(G, u) + HTw)
-    dMs = np.sum(m * hw, axis=-1) - np.sum(w * (hex_ + hu), axis=-1) * inv
+    dMs = np.sum(m * hw, axis=-1) - np.sum(w * (hex_ + hu + hd), axis=-1) * inv
     gMs = -gp * dMs
     lam = lam * ok[..., None]
     gMs = gMs * ok
