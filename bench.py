@@ -1010,7 +1010,7 @@ def main():
     ap.add_argument("--nz", type=int, default=0,
                     help="profiling case: the bulk workload cropped to nz planes (the printed line is not a bench "
                          "result)")
-    ap.add_argument("--serve-requests", type=int, default=32,
+    ap.add_argument("--serve-requests", type=int, default=512,
                     help="requests of the served stream to run (512 = all; 0 = skip)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="profiling case: only the 192x192x48 mixed-radix grid (the printed line is not a bench "

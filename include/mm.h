@@ -200,11 +200,13 @@ mm_status mm_relax(mm_state* s, double tol, int max_steps, double rtol, double* 
  * and demag settings (renormalisation included):
  *   lambda_n       = (dPhi/dm_n)^T lambda_np1
  *   grad_Ms_accum += (dPhi/dMs)^T lambda_np1   (per cell; NULL to skip)
- * The demag part uses that the convolution is its own transpose.  All four
- * arrays are device memory in the state's layout and real type (grad_Ms_accum
- * has nx*ny*nz values); lambda_n must not alias the inputs.  The step's stage
- * inputs and fields are recomputed from m_n (no forward state is kept).
- * Enqueues only. */
+ * The demag part uses that the convolution is its own transpose, the exchange
+ * and DMI parts that their link sums are symmetric; the precession switch of
+ * mm_set_llg_options is honoured.  All four arrays are device memory in the
+ * state's layout and real type (grad_Ms_accum has nx*ny*nz values); lambda_n
+ * must not alias the inputs.  The step's stage inputs and fields are
+ * recomputed from m_n (no forward state is kept).  MM_EINVAL for
+ * non-equidistant layers (not covered).  Enqueues only. */
 mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_np1, void* lambda_n,
                               void* grad_Ms_accum, double dt, double t);
 
@@ -273,8 +275,8 @@ mm_status mm_batch_get_m(mm_batch* b, int slot, void* m_out, int on_device);
  * harmonic mean for equal signs; for opposite signs the geometric mean of the
  * geometric and the arithmetic mean, with the sign of the sum).  Its energy
  * is the fifth entry of mm_heff's E_out.  MM_DMI_NONE switches the term off.
- * The adjoint does not cover DMI (mm_llg_step_adjoint returns MM_EINVAL).
- * MM_EINVAL for an unknown kind or a non-finite D. */
+ * mm_llg_step_adjoint differentiates through it.  MM_EINVAL for an unknown
+ * kind or a non-finite D. */
 mm_status mm_set_dmi(mm_state* s, mm_dmi_kind kind, double D, const double* D_cell, int on_device);
 
 /* Non-equidistant layers (Sec. 4.4): the grid's nz cells along z become
@@ -300,8 +302,8 @@ mm_status mm_set_layers(mm_state* s, const double* h, int nz);
  * uses (MM_DP45, the default, or MM_RKF45); precession = 0 drops the m x h
  * term of Eq. llg for every integrator of this state (the damping term keeps
  * its factor gamma alpha / (1 + alpha^2)), as for ground-state searches;
- * 1 (the default) restores it.  mm_llg_step_adjoint needs precession = 1
- * (MM_EINVAL otherwise).  MM_EINVAL for other values. */
+ * 1 (the default) restores it; mm_llg_step_adjoint follows the setting.
+ * MM_EINVAL for other values. */
 mm_status mm_set_llg_options(mm_state* s, mm_method relax_method, int precession);
 
 /* Diagnostic (the paper has no counterpart): enqueue on the state's stream

@@ -1,15 +1,18 @@
 // Hand-written discrete adjoint of one RK4 step (the gradient Sec. 5.2 gets
 // from autograd), per cell, for the LLG right-hand side of Eq. llg:
 //
-//   f(m) = -g' [m x h + a m x (m x h)],  h = H m + h_ext,  g' = gamma/(1+a^2)
-//   for a cotangent u of f:  v = u + a (u x m),  w = v x m,  G = m x h
+//   f(m) = -g' [p m x h + a m x (m x h)],  h = H m + h_ext,  g' = gamma/(1+a^2),
+//   p = 1 with the precession term, 0 without it (Sec. 3)
+//   for a cotangent u of f:  v = p u + a (u x m),  w = v x m,  G = m x h
 //   (df/dm)^T u  = -g' [h x v + a G x u + H^T w]
-//   (df/dMs)^T u = -g' [m . hw - w . (h_ex + h_u) / Ms]      (per cell)
+//   (df/dMs)^T u = -g' [m . hw - w . (h_ex + h_dmi + h_u) / Ms]      (per cell)
 //
 // with hw = -N * w (the demag convolution is symmetric and even, so its
-// transpose is itself), H^T w = Ms hw + (2/mu0) S(w/Ms) + h_u(w), S the
+// transpose is itself), H^T w = Ms hw + (2/mu0) (S + Q)(w/Ms) + h_u(w), S the
 // exchange link sum (the exchange operator is diag(2/(mu0 Ms)) times a
-// symmetric graph Laplacian), h_u symmetric per cell.
+// symmetric graph Laplacian), Q the DMI link sum (Sec. 4.3: cell i gets
+// Dt e_k x m_{i+k} / (2 d) from each neighbour, with e_{-k} = -e_k, which
+// makes Q symmetric too), h_u symmetric per cell.
 #include "adjoint.h"
 
 namespace mm {
@@ -17,6 +20,23 @@ namespace mm {
 template <typename T> __device__ __forceinline__ T hmean(T a, T b) {
     const T s = a + b;
     return s != (T)0 ? (T)2 * a * b / s : (T)0;
+}
+
+// Eq. D_avg as read (the forward field's link average): harmonic mean for
+// equal signs, otherwise the geometric mean of the geometric and the
+// arithmetic mean with the sign of the sum
+template <typename T> __device__ __forceinline__ T adj_dmi_avg(T a, T b) {
+    const T prod = a * b, s = a + b;
+    if (prod >= (T)0) return s != (T)0 ? (T)2 * prod / s : (T)0;
+    return copysign(sqrt(sqrt(-prod) * fabs(s) * (T)0.5), s);
+}
+
+// out += c e x (a, b, d)
+template <typename T> __device__ __forceinline__ void adj_cross_add(const T* e, T c, T a, T b, T d, T& ox, T& oy,
+                                                                    T& oz) {
+    ox += c * (e[1] * d - e[2] * b);
+    oy += c * (e[2] * a - e[0] * d);
+    oz += c * (e[0] * b - e[1] * a);
 }
 
 template <typename T> __device__ __forceinline__ void axis_of(const AdjParams<T>& p, int i, T& ex, T& ey, T& ez) {
@@ -37,8 +57,9 @@ template <typename T> __global__ void adj_prep_kernel(AdjParams<T> p) {
     const T Ms = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
     const T al = p.alpha_cell ? p.alpha_cell[i] : p.alpha;
     const T gp = (T)kGamma / ((T)1 + al * al);
-    // v = u + a u x m ; w = v x m ; G = m x h
-    const T vx = ux + al * (uy * mz - uz * my), vy = uy + al * (uz * mx - ux * mz), vz = uz + al * (ux * my - uy * mx);
+    // v = p u + a u x m ; w = v x m ; G = m x h
+    const T vx = p.pc * ux + al * (uy * mz - uz * my), vy = p.pc * uy + al * (uz * mx - ux * mz),
+            vz = p.pc * uz + al * (ux * my - uy * mx);
     const T wx = vy * mz - vz * my, wy = vz * mx - vx * mz, wz = vx * my - vy * mx;
     const T Gx = my * hz - mz * hy, Gy = mz * hx - mx * hz, Gz = mx * hy - my * hx;
     // h x v + a G x u
@@ -83,6 +104,24 @@ template <typename T> __global__ void adj_finish_kernel(AdjParams<T> p) {
         MM_ALINK(z > 0, -p.nx * p.ny, p.idz2)
         MM_ALINK(z < p.nz - 1, p.nx * p.ny, p.idz2)
 #undef MM_ALINK
+        // DMI link sums Q q and Q m (the neighbour k's term is Dt e_k x v_k / (2 d), e_{-k} = -e_k)
+        T Dqx = 0, Dqy = 0, Dqz = 0, Dmx = 0, Dmy = 0, Dmz = 0;
+        if (p.dmi) {
+            const T Di = p.D_cell ? p.D_cell[i] : p.D;
+            auto dlink = [&](bool cond, int off, T sgn, const T* e, T i2d) {
+                if (!cond) return;
+                const int k = i + off;
+                const T c = sgn * (p.D_cell ? adj_dmi_avg(Di, p.D_cell[k]) : p.D) * i2d;
+                adj_cross_add(e, c, p.q[k], p.q[N + k], p.q[2 * N + k], Dqx, Dqy, Dqz);
+                adj_cross_add(e, c, p.m[k], p.m[N + k], p.m[2 * N + k], Dmx, Dmy, Dmz);
+            };
+            dlink(x > 0, -1, (T)-1, &p.dmi_e[0], p.i2dx);
+            dlink(x < p.nx - 1, 1, (T)1, &p.dmi_e[0], p.i2dx);
+            dlink(y > 0, -p.nx, (T)-1, &p.dmi_e[3], p.i2dy);
+            dlink(y < p.ny - 1, p.nx, (T)1, &p.dmi_e[3], p.i2dy);
+            dlink(z > 0, -p.nx * p.ny, (T)-1, &p.dmi_e[6], p.i2dz);
+            dlink(z < p.nz - 1, p.nx * p.ny, (T)1, &p.dmi_e[6], p.i2dz);
+        }
         const T wx = p.w[i], wy = p.w[N + i], wz = p.w[2 * N + i];
         const T hwx = p.hw ? p.hw[i] : (T)0, hwy = p.hw ? p.hw[N + i] : (T)0, hwz = p.hw ? p.hw[2 * N + i] : (T)0;
         T ex, ey, ez;
@@ -92,13 +131,14 @@ template <typename T> __global__ void adj_finish_kernel(AdjParams<T> p) {
         const T ew = ex * wx + ey * wy + ez * wz, em = ex * mx + ey * my + ez * mz;
         const T c2 = (T)(2.0 / kMu0);
         // H^T w
-        const T tx = Ms * hwx + c2 * Sqx + cu * ew * ex;
-        const T ty = Ms * hwy + c2 * Sqy + cu * ew * ey;
-        const T tz = Ms * hwz + c2 * Sqz + cu * ew * ez;
+        const T tx = Ms * hwx + c2 * (Sqx + Dqx) + cu * ew * ex;
+        const T ty = Ms * hwy + c2 * (Sqy + Dqy) + cu * ew * ey;
+        const T tz = Ms * hwz + c2 * (Sqz + Dqz) + cu * ew * ez;
         lx -= gp * tx; ly -= gp * ty; lz -= gp * tz;
-        // d<w,h>/dMs = m.hw - w.(h_ex + h_u)/Ms
+        // d<w,h>/dMs = m.hw - w.(h_ex + h_dmi + h_u)/Ms
         const T hex = c2 * inv, hu = cu * em;
-        const T wh = wx * (hex * Smx + hu * ex) + wy * (hex * Smy + hu * ey) + wz * (hex * Smz + hu * ez);
+        const T wh = wx * (hex * (Smx + Dmx) + hu * ex) + wy * (hex * (Smy + Dmy) + hu * ey) +
+                     wz * (hex * (Smz + Dmz) + hu * ez);
         const T dMs = (mx * hwx + my * hwy + mz * hwz) - wh * inv;
         if (p.gMs) p.gMs[i] += -gp * dMs;
     }

@@ -26,6 +26,13 @@ template <typename T> struct AdjParams {
     T* u_prev;       // dt b_{s-1} lambda_y + dt c_s lambda_s (null for the first stage)
     const T* lam_y;
     T cb, cc;        // dt b_{s-1}, dt c_s
+    T pc;            // 1 with the precession term of Eq. llg, 0 without it
+    // DMI (Sec. 4.3): on, uniform D or per-cell D_cell (links averaged as in
+    // the forward field), the DMI vectors e_x, e_y, e_z and 1 / (2 d) per axis
+    int dmi;
+    const T* D_cell; T D;
+    T dmi_e[9];
+    T i2dx, i2dy, i2dz;
 };
 
 }  // namespace mm

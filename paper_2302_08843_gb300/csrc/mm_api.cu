@@ -637,6 +637,15 @@ mm_status adjoint_impl(mm_state* s, const void* m_n, const void* lam_np1, void* 
         p.lam_y = Aly;
         p.cb = st > 0 ? (T)(dt * b[st - 1]) : (T)0;
         p.cc = (T)(dt * kRK4_C[st]);
+        p.pc = s->precession ? (T)1 : (T)0;
+        {
+            StageParams<T> fp;     // the forward field's DMI settings
+            fill_common<T>(s, fp, ms[st], t);
+            p.dmi = fp.dmi;
+            p.D_cell = fp.D_cell; p.D = fp.D;
+            for (int q = 0; q < 9; ++q) p.dmi_e[q] = fp.dmi_e[q];
+            p.i2dx = fp.i2dx; p.i2dy = fp.i2dy; p.i2dz = fp.i2dz;
+        }
         launch_adj_prep<T>(p, s->st);
         MM_LAUNCHED();
         if (!s->demag_off) {
@@ -1246,10 +1255,7 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
     if (!m_n || !lambda_np1 || !lambda_n) return fail(MM_EINVAL, "null m_n, lambda_np1 or lambda_n");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MM_EINVAL, "dt must be > 0");
     if (lambda_n == lambda_np1 || lambda_n == m_n) return fail(MM_EINVAL, "lambda_n must not alias the inputs");
-    if (!s->precession) return fail(MM_EINVAL, "the adjoint is written for the LLG right-hand side with precession");
     if (!s->lay_h.empty()) return fail(MM_EINVAL, "the adjoint does not cover non-equidistant layers");
-    if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell))
-        return fail(MM_EINVAL, "the adjoint does not cover the DMI term");
     MM_TRY(ready_for_fields(s));
     MM_TRY(set_device(s));
     return s->prec == MM_FP64 ? adjoint_impl<double>(s, m_n, lambda_np1, lambda_n, grad_Ms_accum, dt, t)

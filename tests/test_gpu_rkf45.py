@@ -1,7 +1,7 @@
 """GPU parity of the Runge-Kutta-Fehlberg 4(5) integrator (the paper's
 default solver, Sec. 3) and of the LLG without the precession term: accepted
 step sizes and states against the oracle, relaxation without precession, the
-fused FP32 RK4 path with the term switched off, and the adjoint's refusal."""
+fused FP32 RK4 path with the term switched off, and the adjoint without it."""
 import numpy as np
 import pytest
 
@@ -94,16 +94,31 @@ def test_rk4_without_precession(precision, tol):
     s.close()
 
 
-def test_adjoint_needs_precession():
+def test_adjoint_without_precession_matches_oracle():
+    """One RK4 step's adjoint with the precession term switched off, against
+    the oracle's FP64 adjoint of the same right-hand side."""
     import torch
-    from paper_2302_08843_gb300 import workloads as W
-    from paper_2302_08843_gb300.binding import MMError, STATUS_NAMES, setup_workload
-    w = W.plain_fp64()
-    s = setup_workload(w, "fp64")
+    from oracle.adjoint import rk4_step_vjp
+    from oracle.constants import MU0
+    from oracle.llg import Problem, normalize
+    from paper_2302_08843_gb300.binding import State
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    n, d = (8, 6, 3), (3e-9, 2.5e-9, 3e-9)
+    rng = np.random.default_rng(41)
+    Ms = rng.uniform(5e5, 1e6, size=n)
+    m = normalize(rng.normal(size=n + (3,)))
+    lam1 = rng.normal(size=n + (3,))
+    h = (0.02 / MU0, 0.01 / MU0, 0.0)
+    prob = Problem(n, d, Ms=Ms, A=1.3e-11, alpha=0.3, Ku1=2e5, ku_axis=(0.0, 0.6, 0.8), h_ext=h, precession=False)
+    dt, t = 5e-14, 0.0
+    lam_ref, g_ref = rk4_step_vjp(prob, m, t, dt, lam1)
+    s = State(n, d, "fp64")
+    s.set_material(Ms=0.0, A=1.3e-11, alpha=0.3, Ku1=2e5, ku_axis=(0.0, 0.6, 0.8), Ms_cell=to_soa(Ms))
+    s.set_zeeman(h=h)
     s.set_llg_options(precession=False)
-    m = s.get_m().clone()
-    lam = torch.zeros_like(m)
-    with pytest.raises(MMError) as e:
-        s.step_adjoint(m, lam, w.dt)
-    assert STATUS_NAMES[e.value.status] == "MM_EINVAL"
+    s.demag_setup(20)
+    gMs = torch.zeros((n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
+    lam = s.step_adjoint(to_soa(m), to_soa(lam1), dt, t, grad_Ms=gMs)
+    assert rel(from_soa(to_host(lam)), lam_ref) < 1e-9
+    assert rel(from_soa(to_host(gMs)), g_ref) < 1e-9
     s.close()
