@@ -348,7 +348,8 @@ def traffic_for(kernel, precision):
 
 # the files that define the timed FP32 stage kernels (device code and the
 # launch configuration); a change to any of them invalidates stored counters
-KERNEL_SOURCES = ("demag_passes.cu", "fft_engine.cuh", "fft_pair.cuh", "common.cuh", "tma.cuh", "demag.h")
+KERNEL_SOURCES = ("demag_passes.cu", "demag_rt.cu", "fft_engine.cuh", "fft_pair.cuh", "common.cuh", "tma.cuh",
+                  "demag.h")
 
 
 def source_hash():
@@ -773,6 +774,31 @@ def serve_measure(torch, n_requests, dist=None, rank=0, ws=1):
     summ["per_solve"] = {prec: {"cell_steps_per_s": v[0] / v[1],
                                 "sample": "100 DP45 steps of mm_relax on one request of each shape"}
                          for prec, v in per.items()}
+    # batched rate per shape with every slot running (no admission, no host
+    # loop): what the device sustains for each bucket, against the served rate
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.serving import auto_capacity
+    batch_rate = {}
+    for shp in W.SERVING_GRIDS:
+        rq = [w for _, w in stream if tuple(w.n) == tuple(shp)]
+        cap = auto_capacity(shp)
+        b = Batch(shp, rq[0].dx, "fp32", capacity=cap)
+        for sl in range(cap):
+            w = rq[sl % len(rq)]
+            b.set_slot(sl, w.Ms, w.A, w.alpha, W.to_soa(w.m0).astype(np.float32))
+        b.begin(16, 1e-5, 1e-30, 10 ** 9)
+        b.end()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            b.begin(16, 1e-5, 1e-30, 10 ** 9)
+            b.end()
+        el = time.perf_counter() - t0
+        cells = cap * int(np.prod(shp))
+        batch_rate["%dx%dx%d" % tuple(shp)] = {"slots": cap, "ms_per_attempt": round(el / 48 * 1e3, 4),
+                                               "cell_attempts_per_s": cells * 48 / el}
+        b.close()
+    summ["batched_rate_by_shape"] = batch_rate
     summ["served_vs_fp64_per_solve"] = summ["cell_steps_per_s"] / summ["per_solve"]["fp64"]["cell_steps_per_s"]
     summ["fp32_field_rel_err_vs_fp64"] = ferr
     return summ

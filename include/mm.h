@@ -330,10 +330,11 @@ mm_status mm_probe_fp64_fma(void* cuda_stream, double* sink, int blocks, int ite
 
 /* Host-only helper (no GPU): the padded FFT extent the library uses along an
  * axis of n cells (Sec. 4.4 zero padding, P >= 2n): 1 for n = 1, otherwise the
- * smallest length >= 2n among the powers of two up to 4096 and the lengths
- * r 2^a the mixed-radix passes transform (r = 3: 96, 192, 384, 768; r = 7:
- * 112, 224, 448, 896; r = 25: 100, 200, 400, 800).
- * 0 for n < 1. */
+ * smallest even 7-smooth length 2^a 3^b 5^c 7^d >= 2n up to 3200, and above
+ * that the next power of two (grids needing more than 4096 are refused by
+ * mm_state_create).  Powers of two and the lengths r 2^a with r = 3, 7, 25
+ * run compiled FFT engines; every other such length runs the runtime-plan
+ * passes.  0 for n < 1. */
 int mm_fft_extent(int n);
 
 /* Host-only helper (no GPU): the real-space demag tensor this library builds

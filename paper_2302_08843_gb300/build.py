@@ -18,7 +18,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_UNITS = ["mm_api.cu", "demag_passes.cu", "llg_kernels.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "diag.cu"]
+CU_UNITS = ["mm_api.cu", "demag_passes.cu", "demag_rt.cu", "llg_kernels.cu", "noalloc.cu", "adjoint.cu", "batch.cu",
+            "diag.cu"]
 CPP_UNITS = ["tensor_host.cpp"]
 
 

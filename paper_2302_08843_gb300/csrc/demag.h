@@ -11,18 +11,28 @@
 
 namespace mm {
 
-// Padded FFT extent of an axis of n cells: 1 for one cell, otherwise the
-// smallest length >= 2n among the powers of two and the 5-smooth lengths the
-// FFT engines support (100, 200, 400, 800).
+// Lengths with a compiled mixed-radix engine (fft_engine.cuh, FftMixed); every
+// other 7-smooth even length up to kMaxFft that is not a power of two runs the
+// runtime-plan passes of demag_rt.cu.
+bool fft_rt_length(int L);
+
+// Padded FFT extent of an axis of n cells (Sec. 4.4 zero padding, P >= 2n):
+// 1 for one cell, otherwise the smallest even 7-smooth length 2^a 3^b 5^c 7^d
+// >= 2n up to kMaxRtFft, beyond that the next power of two (kMaxFft at most;
+// larger values are refused by the callers).  Even lengths keep the
+// two-real-rows packing of the x passes; the bound kMaxRtFft keeps the FP64
+// z pass's four line buffers within shared memory.
+constexpr int kMaxRtFft = 3200;
 inline int fft_extent(int n) {
     if (n <= 1) return 1;
-    const int t = 2 * n;
-    int best = 1;
-    while (best < t) best <<= 1;
-    // the mixed-radix lengths r 2^a (r = 3, 7, 25) of the FFT engine
-    const int mixed[12] = {96, 100, 112, 192, 200, 224, 384, 400, 448, 768, 800, 896};
-    for (int L : mixed)
-        if (L >= t && L < best) best = L;
+    for (int L = 2 * n; L <= kMaxRtFft; L += 2) {
+        int v = L;
+        for (int p : {2, 3, 5, 7})
+            while (v % p == 0) v /= p;
+        if (v == 1) return L;
+    }
+    int best = 1;       // beyond: the next power of two (above kMaxFft: refused by the callers)
+    while (best < 2 * n) best <<= 1;
     return best;
 }
 
@@ -71,6 +81,20 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
 template <typename T>
 void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool need_p1, typename Cplx<T>::type* S1,
                  typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm);
+
+// runtime-plan passes for the lengths fft_rt_length accepts (demag_rt.cu)
+template <typename T>
+void launch_rt_x_fwd(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typename Cplx<T>::type* S1,
+                     cudaStream_t st);
+template <typename T>
+void launch_rt_x_inv(const DemagDims& d, const typename Cplx<T>::type* S1, T* h, cudaStream_t st);
+template <typename T, int DIR>
+void launch_rt_y(const DemagDims& d, const typename Cplx<T>::type* in, typename Cplx<T>::type* out,
+                 cudaStream_t st);
+template <typename T>
+void launch_rt_z(const DemagDims& d, typename Cplx<T>::type* S2, const T* tens, cudaStream_t st);
+// copy the runtime-plan lengths' twiddle tables to the current device
+cudaError_t upload_twiddles_rt();
 
 // diagnostic: one CTA whose bounded wait on a never-completed mbarrier runs out
 void launch_diag_wait(int* err, unsigned spins, cudaStream_t st);

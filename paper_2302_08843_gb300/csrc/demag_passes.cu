@@ -322,15 +322,37 @@ p5_x_tma(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float* __restr
 // every 32 elements puts the exchange writes of its span-2 pass, 32 elements
 // apart per thread pair, on different banks (123.7 -> 119.5 us on the bulk grid)
 constexpr int kK5Skew = 6;
-template <int LX, int LS> __host__ __device__ constexpr int k5_work_elems() { return LX * LS + (LX / 32) * kK5Skew; }
+template <int LX, int LS> __host__ __device__ constexpr int k5_work_elems() {
+    return LX * LS + (is_pow2(LX) ? (LX / 32) * kK5Skew : 0);
+}
+// the fused kernel's engines: radix-16 with the work-area skew for powers of
+// two, the shared-memory mixed-radix engine for the compiled r 2^a lengths
+template <int LX, int DIR, bool ZIN> struct K5Eng {
+    using type = typename std::conditional<is_pow2(LX), FftLine16<float, (LX < 16 ? 16 : LX), DIR, ZIN, kK5Skew>,
+                                           FftMixed<float, LX, DIR, ZIN>>::type;
+};
 
-template <int LX, int TY, int NSLOT, int PAD, int MINB, bool DMI>
-__global__ void __launch_bounds__((3 * TY / 2) * Fft<float, LX, +1, false>::TPL, MINB)
+// link A of two cells (harmonic mean; zero if both are zero) and, across
+// non-equidistant layers of thickness ha, hb, the two half cells in series
+__device__ __forceinline__ float k5_harm(float a, float b) {
+    const float s = a + b;
+    return s != 0.f ? __fdividef(2.f * a * b, s) : 0.f;
+}
+__device__ __forceinline__ float k5_thick(float a, float b, float ha, float hb) {
+    const float s = ha * b + hb * a;
+    return s != 0.f ? __fdividef((ha + hb) * a * b, s) : 0.f;
+}
+
+// MAT: per-cell Ms, A and Ku1 maps (any of them may be absent) and
+// non-equidistant layers (Sec. 4.4, per-layer z links); the x-forward input is
+// then Ms_cell * next, and a cell with Ms = 0 carries no field.
+template <int LX, int TY, int NSLOT, int PAD, int MINB, bool DMI, bool MAT>
+__global__ void __launch_bounds__((3 * TY / 2) * K5Eng<LX, +1, false>::type::TPL, MINB)
 k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __restrict__ S1, StageParams<float> p,
          int kxb, int nboxes, int slot_bytes) {
     using C = float2;
-    using FI = FftLine16<float, LX, +1, false, kK5Skew>;
-    using FF = FftLine16<float, LX, -1, true, kK5Skew>;
+    using FI = typename K5Eng<LX, +1, false>::type;
+    using FF = typename K5Eng<LX, -1, true>::type;
     static_assert(FI::TPL == FF::TPL, "engines must agree on threads per line");
     static_assert(NSLOT == 1 || NSLOT == 2, "one or two TMA slots");
     constexpr int NL = 3 * TY / 2;
@@ -428,6 +450,131 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             }
             const int y = y0 + yy;
             const int i = x0 + nx * (y + ny * z);      // even: float2 aligned (nx even)
+            if constexpr (MAT) {
+                const float2* m2 = reinterpret_cast<const float2*>(m);
+                const int i2 = i >> 1, N2 = N >> 1;
+                const float2 mx = m2[i2], my = m2[N2 + i2], mz = m2[2 * N2 + i2];
+                const float2 Ms = p.Ms_cell ? reinterpret_cast<const float2*>(p.Ms_cell)[i2] : f2s(p.Ms);
+                const float2* A2 = reinterpret_cast<const float2*>(p.A_cell);
+                const float2 A = A2 ? A2[i2] : f2s(p.A);
+                float2 sx, sy, sz;
+                {   // x links: the inner link, then the outer neighbours (absent ones weigh nothing)
+                    const float wi = p.idx2 * (A2 ? k5_harm(A.x, A.y) : p.A);
+                    sx = f2mul(f2s(wi), f2sub(make_float2(mx.y, mx.x), mx));
+                    sy = f2mul(f2s(wi), f2sub(make_float2(my.y, my.x), my));
+                    sz = f2mul(f2s(wi), f2sub(make_float2(mz.y, mz.x), mz));
+                    const bool hl = x0 > 0, hr = x0 + 2 < nx;
+                    const float wl = hl ? p.idx2 * (A2 ? k5_harm(A.x, p.A_cell[i - 1]) : p.A) : 0.f;
+                    const float wr = hr ? p.idx2 * (A2 ? k5_harm(A.y, p.A_cell[i + 2]) : p.A) : 0.f;
+                    const float2 wo = make_float2(wl, wr);
+                    const float2 ox = make_float2(hl ? m[i - 1] : mx.x, hr ? m[i + 2] : mx.y);
+                    const float2 oy = make_float2(hl ? m[N + i - 1] : my.x, hr ? m[N + i + 2] : my.y);
+                    const float2 oz = make_float2(hl ? m[2 * N + i - 1] : mz.x, hr ? m[2 * N + i + 2] : mz.y);
+                    sx = f2fma(wo, f2sub(ox, mx), sx);
+                    sy = f2fma(wo, f2sub(oy, my), sy);
+                    sz = f2fma(wo, f2sub(oz, mz), sz);
+                }
+                // y and z links; across non-equidistant layers the z link is
+                // 2 A_link / (h_k (h_k + h_nb)) with the two half cells in series
+                auto link = [&](bool cond, int off2, float c, bool thick, float hk, float hn) {
+                    if (cond) {
+                        float2 w;
+                        if (A2) {
+                            const float2 An = A2[i2 + off2];
+                            w = thick ? make_float2(c * k5_thick(A.x, An.x, hk, hn), c * k5_thick(A.y, An.y, hk, hn))
+                                      : make_float2(c * k5_harm(A.x, An.x), c * k5_harm(A.y, An.y));
+                        } else {
+                            w = f2s(c * p.A);
+                        }
+                        const float2 a = m2[i2 + off2], b = m2[N2 + i2 + off2], cc = m2[2 * N2 + i2 + off2];
+                        sx = f2fma(w, f2sub(a, mx), sx);
+                        sy = f2fma(w, f2sub(b, my), sy);
+                        sz = f2fma(w, f2sub(cc, mz), sz);
+                    }
+                };
+                link(y > 0, -(nx >> 1), p.idy2, false, 0.f, 0.f);
+                link(y < ny - 1, nx >> 1, p.idy2, false, 0.f, 0.f);
+                if (!p.lay) {
+                    link(z > 0, -((nx * ny) >> 1), p.idz2, false, 0.f, 0.f);
+                    link(z < nz - 1, (nx * ny) >> 1, p.idz2, false, 0.f, 0.f);
+                } else {
+                    const float hk = p.lay[z];
+                    link(z > 0, -((nx * ny) >> 1), p.lay[2 * nz + z], true, hk, p.lay[z > 0 ? z - 1 : z]);
+                    link(z < nz - 1, (nx * ny) >> 1, p.lay[nz + z], true, hk, p.lay[z < nz - 1 ? z + 1 : z]);
+                }
+                const float2* mn2 = reinterpret_cast<const float2*>(p.mn);
+                const float2 nX = mn2[i2], nY = mn2[N2 + i2], nZ = mn2[2 * N2 + i2];
+                float2 aX = f2s(0.f), aY = f2s(0.f), aZ = f2s(0.f);
+                const float* accsrc = p.acc_in ? p.acc_in : (p.nk > 0 ? p.kin[0] : nullptr);
+                if (accsrc) {
+                    const float2* a2 = reinterpret_cast<const float2*>(accsrc);
+                    aX = a2[i2]; aY = a2[N2 + i2]; aZ = a2[2 * N2 + i2];
+                }
+                // 2 / (mu0 Ms) per cell; a cell with Ms = 0 carries no field
+                const float c2 = (float)(2.0 / kMu0);
+                const float2 inv = make_float2(Ms.x != 0.f ? 1.f / Ms.x : 0.f, Ms.y != 0.f ? 1.f / Ms.y : 0.f);
+                const float2 on = make_float2(Ms.x != 0.f ? 1.f : 0.f, Ms.y != 0.f ? 1.f : 0.f);
+                const float2 cex = f2mul(f2s(c2), inv);
+                float2 hx = f2mul(cex, sx), hy = f2mul(cex, sy), hz = f2mul(cex, sz);
+                const float2 Ku = p.Ku_cell ? reinterpret_cast<const float2*>(p.Ku_cell)[i2] : f2s(p.Ku);
+                if (Ku.x != 0.f || Ku.y != 0.f) {
+                    float2 ex = f2s(p.ex), ey = f2s(p.ey), ez = f2s(p.ez);
+                    if (p.grain) {
+                        const int g0 = p.grain[i], g1 = p.grain[i + 1];
+                        ex = make_float2(p.axis_tab[3 * g0], p.axis_tab[3 * g1]);
+                        ey = make_float2(p.axis_tab[3 * g0 + 1], p.axis_tab[3 * g1 + 1]);
+                        ez = make_float2(p.axis_tab[3 * g0 + 2], p.axis_tab[3 * g1 + 2]);
+                    }
+                    const float2 ck = f2mul(f2mul(f2s(c2), Ku), inv);
+                    const float2 c = f2mul(ck, f2fma(ex, mx, f2fma(ey, my, f2mul(ez, mz))));
+                    hx = f2fma(c, ex, hx);
+                    hy = f2fma(c, ey, hy);
+                    hz = f2fma(c, ez, hz);
+                }
+                constexpr int WSP = 2 * LS;
+                float* w0 = reinterpret_cast<float*>(&work[wat(x0) + 0 * (TY / 2) + (yy >> 1)]) + (yy & 1);
+                float* w1 = reinterpret_cast<float*>(&work[wat(x0) + 1 * (TY / 2) + (yy >> 1)]) + (yy & 1);
+                float* w2 = reinterpret_cast<float*>(&work[wat(x0) + 2 * (TY / 2) + (yy >> 1)]) + (yy & 1);
+                hx = f2mul(on, f2add(hx, f2add(make_float2(w0[0], w0[WSP]), f2s(p.hx0))));
+                hy = f2mul(on, f2add(hy, f2add(make_float2(w1[0], w1[WSP]), f2s(p.hy0))));
+                hz = f2mul(on, f2add(hz, f2add(make_float2(w2[0], w2[WSP]), f2s(p.hz0))));
+                const float2 cx = f2sub(f2mul(my, hz), f2mul(mz, hy));
+                const float2 cy = f2sub(f2mul(mz, hx), f2mul(mx, hz));
+                const float2 cz = f2sub(f2mul(mx, hy), f2mul(my, hx));
+                const float2 dx_ = f2sub(f2mul(my, cz), f2mul(mz, cy));
+                const float2 dy_ = f2sub(f2mul(mz, cx), f2mul(mx, cz));
+                const float2 dz_ = f2sub(f2mul(mx, cy), f2mul(my, cx));
+                const float2 al = f2s(p.alpha), gp = f2s(p.gp_u), pc = f2s(p.no_precession ? 0.f : 1.f);
+                const float2 kx = f2mul(gp, f2fma(al, dx_, f2mul(pc, cx)));
+                const float2 ky = f2mul(gp, f2fma(al, dy_, f2mul(pc, cy)));
+                const float2 kz = f2mul(gp, f2fma(al, dz_, f2mul(pc, cz)));
+                if (p.acc_out) {
+                    const float2 ab = f2s(p.acc_bT);
+                    float2* ao = reinterpret_cast<float2*>(p.acc_out);
+                    ao[i2] = p.acc_in ? f2fma(ab, kx, aX) : f2mul(ab, kx);
+                    ao[N2 + i2] = p.acc_in ? f2fma(ab, ky, aY) : f2mul(ab, ky);
+                    ao[2 * N2 + i2] = p.acc_in ? f2fma(ab, kz, aZ) : f2mul(ab, kz);
+                }
+                const float2 c0 = f2s(p.nk > 0 ? p.kcT[0] : 0.f), ckk = f2s(p.ckT), dtv = f2s(p.dtT);
+                float2 a = f2fma(dtv, f2fma(ckk, kx, f2mul(c0, aX)), nX);
+                float2 b = f2fma(dtv, f2fma(ckk, ky, f2mul(c0, aY)), nY);
+                float2 c = f2fma(dtv, f2fma(ckk, kz, f2mul(c0, aZ)), nZ);
+                if (p.renorm) {
+                    const float2 nn = f2fma(a, a, f2fma(b, b, f2mul(c, c)));
+                    const float2 sc = make_float2(nn.x > 0.f ? 1.f / sqrtf(nn.x) : 1.f,
+                                                  nn.y > 0.f ? 1.f / sqrtf(nn.y) : 1.f);
+                    a = f2mul(a, sc); b = f2mul(b, sc); c = f2mul(c, sc);
+                }
+                float2* no = reinterpret_cast<float2*>(p.next);
+                no[i2] = a;
+                no[N2 + i2] = b;
+                no[2 * N2 + i2] = c;
+                const float2 ma = f2mul(Ms, a), mb = f2mul(Ms, b), mc = f2mul(Ms, c);
+                w0[0] = ma.x; w0[WSP] = ma.y;
+                w1[0] = mb.x; w1[WSP] = mb.y;
+                w2[0] = mc.x; w2[WSP] = mc.y;
+                continue;
+            }
             if constexpr (!DMI) {
                 // the two cells of the item are the two lanes of every paired
                 // FP32 instruction (add/sub/mul/fma .f32x2)
@@ -672,7 +819,7 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             const int c = l / (TY / 2), q = l - c * (TY / 2);
             const int ya = y0 + 2 * q, yb = ya + 1;
             const C zk = work[wat(k) + l];
-            const C zm = work[wat((LX - k) & (LX - 1)) + l];
+            const C zm = work[wat(k == 0 ? 0 : LX - k) + l];   // mirror index, any even LX
             if (ya < ny) S1[((long)(c * nz + z) * ny + ya) * d.KXS + k] = mk<C>(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             if (yb < ny) S1[((long)(c * nz + z) * ny + yb) * d.KXS + k] = mk<C>(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
         }
@@ -749,7 +896,7 @@ p_y_tma(DemagDims d, const __grid_constant__ CUtensorMap in_map, float2* __restr
     const int rows_in = DIR < 0 ? d.ny : L;
     const int rows_out = DIR < 0 ? L : d.ny;
     const int nkt = (d.KX + B - 1) / B;
-    const int ntiles = nkt * 3 * d.nz;
+    const int ntiles = nkt * 3 * d.nz * d.nb;      // (grid, component, z) planes of a batch, grid-major
     const uint32_t tile_bytes = (uint32_t)(nboxes * box_rows * B * sizeof(float2));
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -1593,12 +1740,19 @@ template <int L> constexpr bool tma_len() {
     return is_pow2(L) || Fft<float, L, -1, true>::NR <= 12;
 }
 
+// batches (served grids) on the TMA y passes too
+#ifndef MM_BATCH_TMA_Y
+#define MM_BATCH_TMA_Y 0
+#endif
+constexpr bool kBatchTmaY = MM_BATCH_TMA_Y != 0;
+
 template <int L, int DIR>
 static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cudaStream_t st) {
     constexpr int B = b_tma<L>();
     const int rows_in = DIR < 0 ? d.ny : L;
     static_assert(B % 2 == 0, "tile x coordinates must be 16-byte aligned");
-    if (!d.err || d.nb != 1 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
+    if (!d.err || (!kBatchTmaY && d.nb != 1) || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0)
+        return false;
     // the fewest boxes of at most 256 rows, rows split evenly; with several boxes
     // rounded up to 16 rows (each box then starts 128-byte aligned in the slot);
     // the slot holds L rows
@@ -1606,7 +1760,7 @@ static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cud
     const int box_rows = nboxes == 1 ? rows_in : ((rows_in + nboxes - 1) / nboxes + 15) / 16 * 16;
     if (box_rows > 256 || (size_t)nboxes * box_rows > (size_t)L) return false;
     CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)d.KX, (cuuint64_t)rows_in, (cuuint64_t)(3 * d.nz)};
+    const cuuint64_t dims[3] = {(cuuint64_t)d.KX, (cuuint64_t)rows_in, (cuuint64_t)(3 * d.nz * d.nb)};
     const cuuint64_t strides[2] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)rows_in * d.KXS * 8};
     const cuuint32_t box[3] = {(cuuint32_t)B, (cuuint32_t)box_rows, 1};
     if (!encode_3d(&map, in, dims, strides, box)) return false;
@@ -1615,7 +1769,7 @@ static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cud
     const int threads = (B / 2) * FftPair16<L, DIR, (DIR < 0)>::TPL;
     auto k = p_y_tma<L, B, DIR>;
     set_smem(k, sm);
-    const int grid = persistent_grid(k, threads, sm, nkt * 3 * d.nz);
+    const int grid = persistent_grid(k, threads, sm, nkt * 3 * d.nz * d.nb);
     launch_pdl(k, grid, threads, sm, st, d, map, out, box_rows, nboxes);
     return true;
 }
@@ -1779,15 +1933,19 @@ template <typename T, int L> static void launch_x_inv(const DemagDims& d, const 
 // fused K5 launcher (see k5_fused): false if the shape or material does not qualify
 // k5_fused configuration: TMA slots, work-area row padding, resident CTAs per SM
 constexpr int kK5Rows = 2, kK5Slots = 1, kK5Pad = 0, kK5MinBlocks = 8;
+// resident CTAs asked of the register allocator: 8 for the radix-16 engine,
+// 4 for the mixed-radix one (its 12-28 values per thread would spill at 8)
+template <int L> constexpr int k5_minb() { return is_pow2(L) ? kK5MinBlocks : 4; }
 
 template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st) {
     constexpr int TY = kK5Rows;
-    if constexpr (L < 16 || !is_pow2(L)) {
+    if constexpr (L < 16 || !(is_pow2(L) || kTw5 % L == 0)) {
         return false;
     } else {
         if (!d.err || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(S1) & 15) != 0) return false;
-        if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f || p.hd || p.k_out ||
-            p.h_out || p.want_err || p.want_energy || p.want_torque || !p.next || p.nk > 1)
+        const bool mat = p.Ms_cell || p.A_cell || p.Ku_cell || p.lay;
+        if (p.alpha_cell || p.zw || p.D_cell || (!p.Ms_cell && p.Ms == 0.f) || p.hd || p.k_out || p.h_out ||
+            p.want_err || p.want_energy || p.want_torque || !p.next || p.nk > 1 || (mat && p.dmi))
             return false;
         if (d.nx % 2 != 0) return false;
         int nb = 0;
@@ -1802,10 +1960,11 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         const int slot_bytes = (int)(((size_t)nb * w * TY * 3 * sizeof(float2) + 127) / 128 * 128);
         const size_t sm = kK5Slots * (size_t)slot_bytes + (size_t)k5_work_elems<L, NL + kK5Pad>() * sizeof(float2) + 16;
         if (sm > 220 * 1024) return false;
-        auto k = p.dmi ? k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks, true>
-                       : k5_fused<L, TY, kK5Slots, kK5Pad, kK5MinBlocks, false>;
+        auto k = mat ? k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), false, true>
+                 : p.dmi ? k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), true, false>
+                         : k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), false, false>;
         set_smem(k, sm);
-        const int threads = NL * Fft<float, L, +1, false>::TPL;
+        const int threads = NL * K5Eng<L, +1, false>::type::TPL;
         if (threads > 1024) return false;
         const int ntiles = ((d.ny + TY - 1) / TY) * d.nz;
         const int grid = persistent_grid(k, threads, sm, ntiles);
@@ -1842,6 +2001,15 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         case 800: { constexpr int L_ = 800; CALL; } break;   \
         case 896: { constexpr int L_ = 896; CALL; } break;   \
         default: break;                     \
+    }
+
+// the compiled passes for the lengths MM_DISPATCH_L lists, the runtime-plan
+// passes (demag_rt.cu) for every other 7-smooth length
+#define MM_DISPATCH_RT(Lv, CALL, RTCALL) \
+    if (fft_rt_length(Lv)) {             \
+        RTCALL;                          \
+    } else {                             \
+        MM_DISPATCH_L(Lv, CALL);         \
     }
 
 // P2 .. P4: S1 -> S1 through the tensor multiply.  A 2-D grid (nz = 1, Py <= 256)
@@ -1887,6 +2055,12 @@ static void launch_p3_layers(const DemagDims& d, typename Cplx<T>::type* S2, con
     k<<<grid, dim3(kLayCols, kLayRows), sm, st>>>(d, S2, tens);
 }
 
+// largest padded y extent of a 2-D grid (nz = 1) whose y transforms and tensor
+// multiply run as one pass of the z-pass kernel along y (above it the
+// shared-memory kernel along y measured slower than the y passes: 32 served
+// 256x256x1 grids, 2.36 ms against 2.07 ms per Dormand-Prince attempt)
+constexpr int k2dMaxPy = 256;
+
 template <typename T>
 static void yzy(const DemagDims& d, typename Cplx<T>::type* S1, typename Cplx<T>::type* S2, const T* tens,
                 cudaStream_t st, KernelTimer* tm) {
@@ -1895,7 +2069,7 @@ static void yzy(const DemagDims& d, typename Cplx<T>::type* S1, typename Cplx<T>
         C* S2l = d.LY == 1 ? S1 : S2;
         if (d.LY > 1) {
             tm->begin(st, "p2_y_forward");
-            MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
+            MM_DISPATCH_RT(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)), (launch_rt_y<T, -1>(d, S1, S2, st)));
             tm->end(st);
         }
         tm->begin(st, "p3_layers");
@@ -1903,31 +2077,31 @@ static void yzy(const DemagDims& d, typename Cplx<T>::type* S1, typename Cplx<T>
         tm->end(st);
         if (d.LY > 1) {
             tm->begin(st, "p4_y_inverse");
-            MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
+            MM_DISPATCH_RT(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)), (launch_rt_y<T, +1>(d, S2, S1, st)));
             tm->end(st);
         }
         return;
     }
-    if (d.nz == 1 && d.LY > 1 && d.LY <= 256) {
+    if (d.nz == 1 && d.LY > 1 && d.LY <= k2dMaxPy) {
         DemagDims d2 = d;
         d2.ny = 1; d2.nz = d.ny; d2.LY = 1; d2.LZ = d.LY; d2.yz_swap = 1;
         tm->begin(st, "p3_z_conv");
-        MM_DISPATCH_L(d2.LZ, (launch_p3<T, L_>(d2, S1, tens, st)));
+        MM_DISPATCH_RT(d2.LZ, (launch_p3<T, L_>(d2, S1, tens, st)), (launch_rt_z<T>(d2, S1, tens, st)));
         tm->end(st);
         return;
     }
     C* S2e = d.LY == 1 ? S1 : S2;
     if (d.LY > 1) {
         tm->begin(st, "p2_y_forward");
-        MM_DISPATCH_L(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)));
+        MM_DISPATCH_RT(d.LY, (launch_y<T, L_, -1>(d, S1, S2, st)), (launch_rt_y<T, -1>(d, S1, S2, st)));
         tm->end(st);
     }
     tm->begin(st, "p3_z_conv");
-    MM_DISPATCH_L(d.LZ, (launch_p3<T, L_>(d, S2e, tens, st)));
+    MM_DISPATCH_RT(d.LZ, (launch_p3<T, L_>(d, S2e, tens, st)), (launch_rt_z<T>(d, S2e, tens, st)));
     tm->end(st);
     if (d.LY > 1) {
         tm->begin(st, "p4_y_inverse");
-        MM_DISPATCH_L(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)));
+        MM_DISPATCH_RT(d.LY, (launch_y<T, L_, +1>(d, S2, S1, st)), (launch_rt_y<T, +1>(d, S2, S1, st)));
         tm->end(st);
     }
 }
@@ -1937,11 +2111,11 @@ void demag_apply(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, typenam
                  typename Cplx<T>::type* S2, const T* tens, T* h, cudaStream_t st, KernelTimer* tm) {
     // With ny == 1 the y passes are the identity and S2 aliases S1.
     tm->begin(st, "p1_x_forward");
-    MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
+    MM_DISPATCH_RT(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)), (launch_rt_x_fwd<T>(d, m, Ms_cell, Ms, S1, st)));
     tm->end(st);
     yzy<T>(d, S1, S2, tens, st, tm);
     tm->begin(st, "p5_x_inverse");
-    MM_DISPATCH_L(d.LX, (launch_x_inv<T, L_>(d, S1, h, st)));
+    MM_DISPATCH_RT(d.LX, (launch_x_inv<T, L_>(d, S1, h, st)), (launch_rt_x_inv<T>(d, S1, h, st)));
     tm->end(st);
 }
 
@@ -1950,7 +2124,7 @@ void demag_front(const DemagDims& d, const T* m, const T* Ms_cell, T Ms, bool ne
                  typename Cplx<T>::type* S2, const T* tens, cudaStream_t st, KernelTimer* tm) {
     if (need_p1) {
         tm->begin(st, "p1_x_forward");
-        MM_DISPATCH_L(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)));
+        MM_DISPATCH_RT(d.LX, (launch_x_fwd<T, L_>(d, m, Ms_cell, Ms, S1, st)), (launch_rt_x_fwd<T>(d, m, Ms_cell, Ms, S1, st)));
         tm->end(st);
     }
     yzy<T>(d, S1, S2, tens, st, tm);
@@ -1965,9 +2139,10 @@ bool fused_stage(const DemagDims& d, float2* S1, const StageParams<float>& p, cu
 }
 
 bool fused_stage_supported(const DemagDims& d, const StageParams<float>& p) {
-    if (d.layers || p.lay) return false;
-    if (!d.err || d.LX < 16 || d.LX > 4096 || !is_pow2(d.LX) || d.nx % 2 != 0) return false;
-    if (p.Ms_cell || p.A_cell || p.Ku_cell || p.alpha_cell || p.zw || p.D_cell || p.Ms == 0.f) return false;
+    if (!d.err || d.LX < 16 || d.LX > 4096 || d.nx % 2 != 0) return false;
+    if (fft_rt_length(d.LX)) return false;        // compiled engines only (powers of two, r 2^a)
+    if (p.alpha_cell || p.zw || p.D_cell || (!p.Ms_cell && p.Ms == 0.f)) return false;
+    if ((p.Ms_cell || p.A_cell || p.Ku_cell || p.lay) && p.dmi) return false;
     const int threads = (3 * kK5Rows / 2) * (d.LX / 16);
     return threads <= 1024;
 }

@@ -293,6 +293,7 @@ struct FftMixed {
 
     static __device__ __forceinline__ int in_index(int j, int r) { return j + r * TPL; }
     static __host__ __device__ constexpr bool in_live(int r) { return !ZIN || r < NR / 2; }
+    static __device__ __forceinline__ int at(int e, int LS) { return e * LS; }   // shared-memory place of element e
     static __device__ void tw_build(C*, int, int) {}
 
     template <int P, int NS>

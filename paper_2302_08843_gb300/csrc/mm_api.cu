@@ -87,6 +87,7 @@ cudaError_t ensure_twiddles_on(int dev) {
         built = true;
     }
     cudaError_t e = upload_twiddles(g_tw_host64, g_tw_host32, g_tw5_host64, g_tw5_host32);
+    if (e == cudaSuccess) e = upload_twiddles_rt();
     if (e == cudaSuccess) g_tw_done[dev] = true;
     return e;
 }

@@ -1,9 +1,10 @@
 """GPU parity of the demag field (Sec. 4.4): the five FFT passes of libmm.so
 against the oracle's convolution, element by element, FP64 and FP32, on grids
-that cover one cell, 1-D and 2-D lines, ragged extents that pad beyond 2n,
-every mixed-radix padded length r 2^a (r = 3: 96 ... 768, r = 7: 112 ... 896,
-r = 25: 100 ... 800) on at least one axis, several CTA tiles with ragged
-tails, and the largest padded extent (4096)."""
+that cover one cell, 1-D and 2-D lines, ragged extents, every compiled
+mixed-radix padded length r 2^a (r = 3: 96 ... 768, r = 7: 112 ... 896,
+r = 25: 100 ... 800) on at least one axis, runtime-plan 7-smooth lengths with
+every radix (2, 3, 4, 5, 7) on every axis up to 3000, several CTA tiles with
+ragged tails, and the largest padded extent (4096)."""
 import numpy as np
 import pytest
 
@@ -27,8 +28,10 @@ GRIDS = [
     ((6, 5, 40), (2e-9, 2e-9, 2e-9)),
     ((2048, 2, 1), (1e-9, 1e-9, 1e-9)),
     ((200, 6, 2), (2e-9, 2e-9, 2e-9)),          # x padded to 400
-    ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 768
-    ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 384
+    ((380, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 768
+    ((300, 4, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 600 (runtime plan)
+    ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 300 (runtime plan)
+    ((12, 190, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 384
     ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 96
     ((512, 3, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 1024
     ((1024, 2, 1), (2e-9, 2e-9, 2e-9)),         # x padded to 2048
@@ -52,22 +55,58 @@ GRIDS = [
     ((2, 1, 448), (2e-9, 2e-9, 2e-9)),          # z 896
     # FP32 TMA z pass on 3 x 2^a lines (also as the 2-D path along y), and
     # TMA y tiles split into several boxes of uneven rows
-    ((5, 40, 1), (2e-9, 2e-9, 2e-9)),           # y 96, 2-D
-    ((4, 90, 1), (2e-9, 2e-9, 2e-9)),           # y 192, 2-D
-    ((3, 300, 2), (2e-9, 2e-9, 2e-9)),          # y 768
-    ((2, 450, 2), (2e-9, 2e-9, 2e-9)),          # y 1024: forward 2 boxes of 240 rows
+    ((5, 40, 1), (2e-9, 2e-9, 2e-9)),           # y 80, 2-D (runtime plan)
+    ((5, 48, 1), (2e-9, 2e-9, 2e-9)),           # y 96, 2-D
+    ((4, 90, 1), (2e-9, 2e-9, 2e-9)),           # y 180, 2-D (runtime plan)
+    ((4, 96, 1), (2e-9, 2e-9, 2e-9)),           # y 192, 2-D
+    ((3, 300, 2), (2e-9, 2e-9, 2e-9)),          # y 600 (runtime plan)
+    ((2, 450, 2), (2e-9, 2e-9, 2e-9)),          # y 900 (runtime plan)
+    ((2, 510, 2), (2e-9, 2e-9, 2e-9)),          # y 1024: forward 2 boxes of 256 rows
+    # 2-D grids whose padded y extent is above 256
+    ((6, 250, 1), (2e-9, 2e-9, 2e-9)),          # y 500, 2-D
+    ((6, 256, 1), (2e-9, 2e-9, 2e-9)),          # y 512, 2-D
+    ((5, 180, 1), (2e-9, 2e-9, 2e-9)),          # y 360, 2-D
+    ((3, 700, 1), (2e-9, 2e-9, 2e-9)),          # y 1400, 2-D
+    # runtime-plan lengths (every 7-smooth length without a compiled engine), each radix
+    ((35, 3, 2), (2e-9, 2e-9, 2e-9)),           # x 70 = 2 5 7
+    ((3, 45, 2), (2e-9, 2e-9, 2e-9)),           # y 90 = 2 3^2 5
+    ((4, 3, 27), (2e-9, 2e-9, 2e-9)),           # z 54 = 2 3^3
+    ((5, 63, 1), (2e-9, 2e-9, 2e-9)),           # y 126 = 2 3^2 7, 2-D
+    ((1500, 2, 1), (2e-9, 2e-9, 2e-9)),         # x 3000 = 2^3 3 5^3
+    ((2, 2, 1400), (2e-9, 2e-9, 2e-9)),         # z 2800 = 2^4 5^2 7
+    ((3, 1500, 1), (2e-9, 2e-9, 2e-9)),         # y 3000, 2-D through the y passes
 ]
 
 
 def test_padded_extents_rule():
+    """The smallest even 7-smooth length >= 2n (up to 3200; beyond that the next
+    power of two), 1 for a single cell."""
     from paper_2302_08843_gb300.binding import padded_extents
-    assert padded_extents((1, 2, 3)) == (1, 4, 8)
+    assert padded_extents((1, 2, 3)) == (1, 4, 6)
     assert padded_extents((50, 64, 100)) == (100, 128, 200)
-    assert padded_extents((150, 200, 300)) == (384, 400, 768)
-    assert padded_extents((401, 2048, 33)) == (896, 4096, 96)
+    assert padded_extents((150, 200, 300)) == (300, 400, 600)
+    assert padded_extents((401, 2048, 33)) == (810, 4096, 70)
     assert padded_extents((48, 56, 96)) == (96, 112, 192)
-    assert padded_extents((49, 57, 97)) == (100, 128, 200)
-    assert padded_extents((112, 224, 449)) == (224, 448, 1024)
+    assert padded_extents((49, 57, 97)) == (98, 120, 196)
+    assert padded_extents((35, 45, 27)) == (70, 90, 54)
+    assert padded_extents((65, 70, 5)) == (140, 140, 10)
+    assert padded_extents((7, 1500, 1400)) == (14, 3000, 2800)
+    assert padded_extents((1601, 1700, 2048)) == (4096, 4096, 4096)
+    for n in range(2, 1601):
+        L = padded_extents((n, 1, 1))[0]
+        v = L
+        for q in (2, 3, 5, 7):
+            while v % q == 0:
+                v //= q
+        assert v == 1 and L % 2 == 0 and L >= 2 * n
+        assert not any(_smooth(w) for w in range(2 * n, L, 2))
+
+
+def _smooth(v):
+    for q in (2, 3, 5, 7):
+        while v % q == 0:
+            v //= q
+    return v == 1
 
 
 def _m(n, seed):

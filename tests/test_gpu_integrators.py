@@ -149,3 +149,81 @@ def test_relax_matches_oracle():
     assert tq < 1e-3 and abs(tq - tq_r) < 1e-6 * tq_r
     assert rel(from_soa(to_host(s.get_m())), mr) < 1e-8
     s.close()
+
+
+def test_rk4_fp32_per_cell_materials_through_the_fused_kernel():
+    """FP32 RK4 with per-cell Ms, A and Ku1 maps (including a cell with
+    Ms = 0) runs the fused stage kernel (checked from the launch record);
+    five steps against the oracle."""
+    from oracle.llg import Problem, normalize, rk4_step
+    from paper_2302_08843_gb300.binding import State
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    n, d = (32, 12, 6), (2.5e-9, 2.5e-9, 3e-9)
+    rng = np.random.default_rng(51)
+    Ms = rng.uniform(5e5, 1.1e6, size=n)
+    Ms[3, 4, 2] = 0.0
+    A = rng.uniform(0.8e-11, 1.6e-11, size=n)
+    Ku = rng.uniform(0.0, 3e5, size=n)
+    m0 = normalize(rng.normal(size=n + (3,)))
+    h = (8000.0, 0.0, 2000.0)
+    s = State(n, d, "fp32")
+    s.set_material(Ms=0.0, A=0.0, alpha=0.2, Ku1=0.0, ku_axis=(0.0, 0.6, 0.8), Ms_cell=to_soa(Ms),
+                   A_cell=to_soa(A), Ku1_cell=to_soa(Ku))
+    s.set_zeeman(h=h)
+    s.demag_setup(20)
+    s.set_m(to_soa(m0))
+    prob = Problem(n, d, Ms=Ms, A=A, alpha=0.2, Ku1=Ku, ku_axis=(0.0, 0.6, 0.8), h_ext=h)
+    s.profile_enable(True)
+    m, t, dt = m0.copy(), 0.0, 5e-14
+    for _ in range(5):
+        m = rk4_step(prob, m, t, dt)
+        t, _ = s.step(dt, t, "rk4")
+    prof = s.profile_read()
+    s.profile_enable(False)
+    assert "k5_fused" in prof and "stage_llg" not in prof, prof
+    assert rel(from_soa(to_host(s.get_m())), m) < 5 * FP32_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("n,variant", [((48, 20, 6), "uniform"), ((56, 12, 4), "cells"), ((100, 16, 2), "dmi")])
+def test_rk4_fp32_mixed_radix_x_through_the_fused_kernel(n, variant):
+    """FP32 RK4 on grids whose padded x line is a compiled mixed-radix length
+    (96 = 3 2^5, 112 = 7 2^4, 200 = 25 2^3) runs the fused stage kernel on the
+    mixed-radix engine (checked from the launch record): uniform material,
+    per-cell maps, and uniform interface DMI; five steps against the oracle."""
+    from oracle.llg import Problem, normalize, rk4_step
+    from paper_2302_08843_gb300.binding import State, padded_extents
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    assert padded_extents(n)[0] in (96, 112, 200)
+    d = (2.5e-9, 2.5e-9, 3e-9)
+    rng = np.random.default_rng(52)
+    m0 = normalize(rng.normal(size=n + (3,)))
+    h = (8000.0, 0.0, 2000.0)
+    s = State(n, d, "fp32")
+    kw = dict(alpha=0.2, ku_axis=(0.0, 0.6, 0.8), h_ext=h)
+    if variant == "cells":
+        Ms = rng.uniform(5e5, 1.1e6, size=n)
+        A = rng.uniform(0.8e-11, 1.6e-11, size=n)
+        Ku = rng.uniform(0.0, 3e5, size=n)
+        s.set_material(Ms=0.0, A=0.0, alpha=0.2, Ku1=0.0, ku_axis=(0.0, 0.6, 0.8), Ms_cell=to_soa(Ms),
+                       A_cell=to_soa(A), Ku1_cell=to_soa(Ku))
+        prob = Problem(n, d, Ms=Ms, A=A, Ku1=Ku, **kw)
+    else:
+        s.set_material(Ms=8e5, A=1.3e-11, alpha=0.2, Ku1=1e5, ku_axis=(0.0, 0.6, 0.8))
+        D = 2e-3 if variant == "dmi" else 0.0
+        if variant == "dmi":
+            s.set_dmi("interface", D)
+        prob = Problem(n, d, Ms=8e5, A=1.3e-11, Ku1=1e5, D=D, dmi="interface", **kw)
+    s.set_zeeman(h=h)
+    s.demag_setup(20)
+    s.set_m(to_soa(m0))
+    s.profile_enable(True)
+    m, t, dt = m0.copy(), 0.0, 5e-14
+    for _ in range(5):
+        m = rk4_step(prob, m, t, dt)
+        t, _ = s.step(dt, t, "rk4")
+    prof = s.profile_read()
+    s.profile_enable(False)
+    assert "k5_fused" in prof and "stage_llg" not in prof, prof
+    assert rel(from_soa(to_host(s.get_m())), m) < 5 * FP32_TOL
+    s.close()

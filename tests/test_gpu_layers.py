@@ -117,6 +117,25 @@ def test_layers_rk4_trajectory(precision, tol):
     s.close()
 
 
+def test_layers_rk4_fp32_through_the_fused_kernel():
+    """FP32 RK4 on a stack with a power-of-two x line runs the fused stage
+    kernel with per-cell materials and per-layer z links (checked from the
+    launch record); five steps against the oracle."""
+    from oracle.llg import rk4_step
+    from paper_2302_08843_gb300.workloads import from_soa
+    w, s, prob = _setup((32, 20, 5), "fp32")
+    s.profile_enable(True)
+    m, t = w.m0.copy(), 0.0
+    for _ in range(5):
+        m = rk4_step(prob, m, t, w.dt)
+        t, _ = s.step(w.dt, t, "rk4")
+    prof = s.profile_read()
+    s.profile_enable(False)
+    assert "k5_fused" in prof and "stage_llg" not in prof, prof
+    assert rel(from_soa(to_host(s.get_m())), m) < 5 * FP32_TOL
+    s.close()
+
+
 def test_layers_dp45_steps():
     """Adaptive steps: the accepted times, step sizes and states follow the oracle."""
     from oracle.llg import dp45_attempt, dp45_factor, normalize
