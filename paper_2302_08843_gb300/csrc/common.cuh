@@ -166,6 +166,23 @@ template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1
     a2 = csub(t, u);
 }
 
+// DFT6 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 6), as two DFT3 of the
+// even and odd inputs: X_k = E_k + W6^k O_k, X_{k+3} = E_k - W6^k O_k (k < 3),
+// W6 = exp(DIR i pi / 3) = (1/2, DIR sqrt(3)/2), W6^2 = (-1/2, DIR sqrt(3)/2)
+template <int DIR, typename C> __device__ __forceinline__ void dft6(C (&a)[6]) {
+    using T = decltype(C::x);
+    constexpr T h = (T)0.86602540378443864676;      // sin(pi / 3)
+    C e0 = a[0], e1 = a[2], e2 = a[4], o0 = a[1], o1 = a[3], o2 = a[5];
+    dft3<DIR>(e0, e1, e2);
+    dft3<DIR>(o0, o1, o2);
+    const T sh = DIR * h;
+    const C w1 = mk<C>((T)0.5 * o1.x - sh * o1.y, (T)0.5 * o1.y + sh * o1.x);     // W6 o1
+    const C w2 = mk<C>((T)-0.5 * o2.x - sh * o2.y, (T)-0.5 * o2.y + sh * o2.x);   // W6^2 o2
+    a[0] = cadd(e0, o0); a[3] = csub(e0, o0);
+    a[1] = cadd(e1, w1); a[4] = csub(e1, w1);
+    a[2] = cadd(e2, w2); a[5] = csub(e2, w2);
+}
+
 // DFT7 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 7), from the pairs
 // p_k = a_k + a_{7-k}, m_k = a_k - a_{7-k} (k = 1, 2, 3):
 // X_q, X_{7-q} = a0 + sum_k p_k cos(2 pi k q / 7) +- DIR i sum_k m_k sin(2 pi k q / 7)

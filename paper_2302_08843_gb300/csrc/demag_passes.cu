@@ -329,7 +329,7 @@ template <int LX, int LS> __host__ __device__ constexpr int k5_work_elems() {
 // two, the shared-memory mixed-radix engine for the compiled r 2^a lengths
 template <int LX, int DIR, bool ZIN> struct K5Eng {
     using type = typename std::conditional<is_pow2(LX), FftLine16<float, (LX < 16 ? 16 : LX), DIR, ZIN, kK5Skew>,
-                                           FftMixed<float, LX, DIR, ZIN>>::type;
+                                           FftMixed<float, LX, DIR, ZIN, false>>::type;
 };
 
 // link A of two cells (harmonic mean; zero if both are zero) and, across
@@ -1740,19 +1740,12 @@ template <int L> constexpr bool tma_len() {
     return is_pow2(L) || Fft<float, L, -1, true>::NR <= 12;
 }
 
-// batches (served grids) on the TMA y passes too
-#ifndef MM_BATCH_TMA_Y
-#define MM_BATCH_TMA_Y 0
-#endif
-constexpr bool kBatchTmaY = MM_BATCH_TMA_Y != 0;
-
 template <int L, int DIR>
 static bool launch_py_tma(const DemagDims& d, const float2* in, float2* out, cudaStream_t st) {
     constexpr int B = b_tma<L>();
     const int rows_in = DIR < 0 ? d.ny : L;
     static_assert(B % 2 == 0, "tile x coordinates must be 16-byte aligned");
-    if (!d.err || (!kBatchTmaY && d.nb != 1) || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0)
-        return false;
+    if (!d.err || d.nb != 1 || (d.KXS * 8) % 16 != 0 || (reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     // the fewest boxes of at most 256 rows, rows split evenly; with several boxes
     // rounded up to 16 rows (each box then starts 128-byte aligned in the slot);
     // the slot holds L rows

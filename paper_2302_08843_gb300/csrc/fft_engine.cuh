@@ -270,23 +270,34 @@ __host__ __device__ constexpr int m5_fives(int L, int r = 0) {
 }
 __host__ __device__ constexpr int m5_powr(int r, int b) { return b == 0 ? 1 : r * m5_powr(r, b - 1); }
 __host__ __device__ constexpr int m5_twos(int L) { return ilog2(L / m5_powr(m5_oddr(L), m5_fives(L))); }
-__host__ __device__ constexpr int m5_npass(int L) {
-    return m5_fives(L) + m5_twos(L) / 2 + m5_twos(L) % 2;
+// Shorter plans where the registers allow them (fewer shared-memory round
+// trips): 96 = 6 4 4 (12 values per thread, as before), 384 = 6 8 8 and
+// 768 = 3 8 8 4 (24 values per thread instead of 12).
+__host__ __device__ constexpr int m5_alt_np(int L) { return L == 96 ? 3 : (L == 384 ? 3 : (L == 768 ? 4 : 0)); }
+__host__ __device__ constexpr int m5_alt_r(int L, int p) {
+    return L == 96 ? (p == 0 ? 6 : 4) : (L == 384 ? (p == 0 ? 6 : 8) : (p == 0 ? 3 : (p < 3 ? 8 : 4)));
 }
-__host__ __device__ constexpr int m5_radix(int L, int p) {
-    return p < m5_fives(L) ? m5_oddr(L) : (p < m5_fives(L) + m5_twos(L) / 2 ? 4 : 2);
+// (ALT = false keeps the radix 4/2 plan, whose 12 values per thread suit the
+// fused stage kernel's small CTAs better.)
+__host__ __device__ constexpr int m5_npass(int L, bool alt = true) {
+    return (alt && m5_alt_np(L)) ? m5_alt_np(L) : m5_fives(L) + m5_twos(L) / 2 + m5_twos(L) % 2;
+}
+__host__ __device__ constexpr int m5_radix(int L, int p, bool alt = true) {
+    return (alt && m5_alt_np(L)) ? m5_alt_r(L, p)
+                                 : (p < m5_fives(L) ? m5_oddr(L) : (p < m5_fives(L) + m5_twos(L) / 2 ? 4 : 2));
 }
 __host__ __device__ constexpr int m5_gcd(int a, int b) { return b == 0 ? a : m5_gcd(b, a % b); }
-__host__ __device__ constexpr int m5_tpl(int L, int p = 0) {
-    return p == m5_npass(L) - 1 ? L / m5_radix(L, p) : m5_gcd(L / m5_radix(L, p), m5_tpl(L, p + 1));
+__host__ __device__ constexpr int m5_tpl(int L, int p = 0, bool alt = true) {
+    return p == m5_npass(L, alt) - 1 ? L / m5_radix(L, p, alt)
+                                     : m5_gcd(L / m5_radix(L, p, alt), m5_tpl(L, p + 1, alt));
 }
 
-template <typename T, int L, int DIR, bool ZIN>
+template <typename T, int L, int DIR, bool ZIN, bool ALT = true>
 struct FftMixed {
     using C = typename Cplx<T>::type;
     static_assert(kTw5 % L == 0, "mixed-radix lengths must divide the twiddle table");
-    static constexpr int NP = m5_npass(L);
-    static constexpr int TPL = m5_tpl(L);
+    static constexpr int NP = m5_npass(L, ALT);
+    static constexpr int TPL = m5_tpl(L, 0, ALT);
     static constexpr int NR = L / TPL;
     static constexpr int NTW = 0;
     static_assert(NR % 2 == 0, "the zero-padded half must be whole registers");
@@ -298,7 +309,7 @@ struct FftMixed {
 
     template <int P, int NS>
     static __device__ __forceinline__ void pass(C* s, int LS, int j) {
-        constexpr int R = m5_radix(L, P);
+        constexpr int R = m5_radix(L, P, ALT);
         constexpr int NB = L / (R * TPL);    // butterflies per thread
         C a[NB][R];
 #pragma unroll
@@ -311,7 +322,9 @@ struct FftMixed {
 #pragma unroll
                 for (int q = 1; q < R; ++q) a[t][q] = cmul(a[t][q], twiddle5<T, DIR>(q * k * (kTw5 / (NS * R))));
             }
-            if constexpr (R == 7) dft7<DIR>(a[t]);
+            if constexpr (R == 8) dft8<DIR>(a[t]);
+            else if constexpr (R == 7) dft7<DIR>(a[t]);
+            else if constexpr (R == 6) dft6<DIR>(a[t]);
             else if constexpr (R == 5) dft5<DIR>(a[t][0], a[t][1], a[t][2], a[t][3], a[t][4]);
             else if constexpr (R == 4) dft4<DIR>(a[t][0], a[t][1], a[t][2], a[t][3]);
             else if constexpr (R == 3) dft3<DIR>(a[t][0], a[t][1], a[t][2]);
