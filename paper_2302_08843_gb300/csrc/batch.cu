@@ -7,12 +7,6 @@
 
 namespace mm {
 
-__device__ __forceinline__ double bwarp_max(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // one thread per cell, grid (ceil(N/256), nb); a masked-off grid does nothing
 template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(BatchStageParams<T> p) {
     const int b = blockIdx.y;
@@ -20,7 +14,12 @@ template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(
     const int N = p.N;
     const int i = blockIdx.x * 256 + threadIdx.x;
     const long off = (long)b * 3 * N;
-    double tq = 0.0, er = 0.0, nf = 0.0;
+    // per thread: the largest |m x h|^2 (the torque's square; sqrt and 1/Ms are
+    // monotone, so they are applied once per warp) and the largest error ratio
+    // |dt e_c| / sc_c, kept as a fraction en / ed (cross-multiplied comparisons,
+    // one division per warp)
+    T tq2 = 0, en = 0, ed = 1;
+    int nf = 0;
     if (i < N) {
         const int x = i % p.nx, yz = i / p.nx, y = yz % p.ny, z = yz / p.ny;
         const T* m = p.m + off;
@@ -44,52 +43,74 @@ template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(
 #undef MM_BLINK
             const T cex = (T)(2.0 / kMu0) / Ms;
             const T* hd = p.hd + off;
-            hx = hd[i] + cex * sx + (T)p.hx0;
-            hy = hd[N + i] + cex * sy + (T)p.hy0;
-            hz = hd[2 * N + i] + cex * sz + (T)p.hz0;
+            hx = hd[i] + cex * sx + p.hx0;
+            hy = hd[N + i] + cex * sy + p.hy0;
+            hz = hd[2 * N + i] + cex * sz + p.hz0;
         }
         const T gp = (T)(-kGamma) / ((T)1 + al * al);
         cx = my * hz - mz * hy; cy = mz * hx - mx * hz; cz = mx * hy - my * hx;
         const T dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
         const T kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
-        if (!(isfinite(kx) && isfinite(ky) && isfinite(kz))) nf = 1.0;
-        if (p.want_torque && Ms != (T)0) tq = sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms;
+        if (!(isfinite(kx) && isfinite(ky) && isfinite(kz))) nf = 1;
+        if (p.want_torque && Ms != (T)0) tq2 = cx * cx + cy * cy + cz * cz;
         if (p.k_out) { T* ko = p.k_out + off; ko[i] = kx; ko[N + i] = ky; ko[2 * N + i] = kz; }
         if (p.next || p.want_err) {
-            const double dt = p.dt[b];
-            T sxn = (T)p.ck * kx, syn = (T)p.ck * ky, szn = (T)p.ck * kz;
-            double ex_ = p.eb_k * kx, ey_ = p.eb_k * ky, ez_ = p.eb_k * kz;
+            const T dt = (T)p.dt[b];
+            T sxn = p.ck * kx, syn = p.ck * ky, szn = p.ck * kz;
+            T ex_ = 0, ey_ = 0, ez_ = 0;
+            if (p.want_err) { ex_ = p.eb_k * kx; ey_ = p.eb_k * ky; ez_ = p.eb_k * kz; }
             for (int q = 0; q < p.nk; ++q) {
                 const T* kq = p.kin[q] + off;
                 const T ax = kq[i], ay = kq[N + i], az = kq[2 * N + i];
-                sxn += (T)p.kc[q] * ax; syn += (T)p.kc[q] * ay; szn += (T)p.kc[q] * az;
+                sxn += p.kc[q] * ax; syn += p.kc[q] * ay; szn += p.kc[q] * az;
                 if (p.want_err) { ex_ += p.eb[q] * ax; ey_ += p.eb[q] * ay; ez_ += p.eb[q] * az; }
             }
             const T* mn = p.mn + off;
             const T m0x = mn[i], m0y = mn[N + i], m0z = mn[2 * N + i];
             if (p.want_err) {
-                const double scx = p.rtol + p.rtol * fmax(fabs((double)m0x), fabs((double)mx));
-                const double scy = p.rtol + p.rtol * fmax(fabs((double)m0y), fabs((double)my));
-                const double scz = p.rtol + p.rtol * fmax(fabs((double)m0z), fabs((double)mz));
-                er = fmax(fmax(fabs(dt * ex_) / scx, fabs(dt * ey_) / scy), fabs(dt * ez_) / scz);
-                if (!isfinite(er)) nf = 1.0;
+                const T scx = p.rtol + p.rtol * fmax(fabs(m0x), fabs(mx));
+                const T scy = p.rtol + p.rtol * fmax(fabs(m0y), fabs(my));
+                const T scz = p.rtol + p.rtol * fmax(fabs(m0z), fabs(mz));
+                const T nx = fabs(dt * ex_), ny = fabs(dt * ey_), nz = fabs(dt * ez_);
+                if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) nf = 1;
+                en = nx; ed = scx;
+                if (ny * ed > en * scy) { en = ny; ed = scy; }
+                if (nz * ed > en * scz) { en = nz; ed = scz; }
             }
             if (p.next) {
                 T* nx_ = p.next + off;
-                nx_[i] = m0x + (T)dt * sxn; nx_[N + i] = m0y + (T)dt * syn; nx_[2 * N + i] = m0z + (T)dt * szn;
+                nx_[i] = m0x + dt * sxn; nx_[N + i] = m0y + dt * syn; nx_[2 * N + i] = m0z + dt * szn;
             }
         }
     }
     if (p.partials) {
-        __shared__ double red[8][3];
+        // maxima in the state's precision; the torque's sqrt and 1/Ms and the
+        // error's division once per block
+        __shared__ T red[8][3];
+        __shared__ int rednf[8];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        tq = bwarp_max(tq); er = bwarp_max(er); nf = bwarp_max(nf);
-        if (lane == 0) { red[wid][0] = tq; red[wid][1] = er; red[wid][2] = nf; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T n2 = __shfl_down_sync(0xffffffffu, en, o), d2 = __shfl_down_sync(0xffffffffu, ed, o);
+            if (n2 * ed > en * d2) { en = n2; ed = d2; }
+            tq2 = fmax(tq2, __shfl_down_sync(0xffffffffu, tq2, o));
+        }
+        const int anynf = __any_sync(0xffffffffu, nf);
+        if (lane == 0) { red[wid][0] = tq2; red[wid][1] = en; red[wid][2] = ed; rednf[wid] = anynf; }
         __syncthreads();
-        if (threadIdx.x < 3) {
-            double a = red[0][threadIdx.x];
-            for (int w = 1; w < 8; ++w) a = fmax(a, red[w][threadIdx.x]);
-            p.partials[((long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = a;
+        if (threadIdx.x == 0) {
+            T t2 = red[0][0], n = red[0][1], d = red[0][2];
+            int f = rednf[0];
+            for (int w = 1; w < 8; ++w) {
+                t2 = fmax(t2, red[w][0]);
+                if (red[w][1] * d > n * red[w][2]) { n = red[w][1]; d = red[w][2]; }
+                f |= rednf[w];
+            }
+            const T Ms = p.Ms[b];
+            double* o = p.partials + ((long)b * gridDim.x + blockIdx.x) * 3;
+            o[0] = Ms != (T)0 ? (double)(sqrt(t2) / Ms) : 0.0;
+            o[1] = (double)(n / d);
+            o[2] = f ? 1.0 : 0.0;
         }
     }
 }

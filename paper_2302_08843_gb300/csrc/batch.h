@@ -13,20 +13,23 @@ template <typename T> struct BatchStageParams {
     const T* alpha;
     const double* dt;         // [nb] per-grid step
     const int* mask;          // [nb] grids this launch works on
-    double hx0, hy0, hz0;     // uniform external field
+    T hx0, hy0, hz0;          // uniform external field
     const T* m;               // stage input [nb][3][N]
     const T* hd;              // demag field [nb][3][N]
     const T* mn;              // m at the start of the step
     T* k_out;
     T* next;                  // mn + dt (sum_j kc_j kin_j + ck k)
     const T* kin[7];
-    double kc[7];
+    // the stage and error coefficients in the state's precision: the error
+    // norm and the torque are evaluated in it (FP64 is a narrow pipe on this
+    // part, and an FP32 state's stage derivatives carry FP32 rounding anyway)
+    T kc[7];
     int nk;
-    double ck;
+    T ck;
     int want_err, want_torque;
-    double eb[7];
-    double eb_k;
-    double rtol;              // atol = rtol
+    T eb[7];
+    T eb_k;
+    T rtol;                   // atol = rtol
     double* partials;         // [nb][blocks per grid][3]
 };
 

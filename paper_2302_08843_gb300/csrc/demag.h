@@ -157,6 +157,10 @@ struct StageParams {
     double* partials;            // [number of blocks][kNPart]
     // the coefficients above in the field type (filled by launch_stage)
     T kcT[7], ckT, dtT, acc_bT;
+    // the error-norm coefficients in the field type: the error norm and the
+    // torque are evaluated in the state's precision (FP64 is a narrow pipe on
+    // this part, and FP32 stage derivatives carry FP32 rounding anyway)
+    T ebT[7], eb_kT, rtolT, atolT;
     T cex_u, cani_u, gp_u;       // 2/(mu0 Ms), 2 Ku/(mu0 Ms), -gamma/(1+alpha^2) for uniform material
 };
 

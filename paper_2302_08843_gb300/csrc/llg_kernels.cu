@@ -107,8 +107,12 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
     const int x0 = (blockIdx.x * kBX + threadIdx.x) * VEC;
     const int y = blockIdx.y * kBY + threadIdx.y;
     const int z = blockIdx.z;
-    double red_torque = 0.0, red_e0 = 0.0, red_e1 = 0.0, red_e2 = 0.0, red_e3 = 0.0, red_e4 = 0.0, red_err = 0.0,
-           red_nf = 0.0;
+    double red_e0 = 0.0, red_e1 = 0.0, red_e2 = 0.0, red_e3 = 0.0, red_e4 = 0.0;
+    int red_nf = 0;
+    // the torque |m x h| / Ms and the error ratio |dt e| / sc, in the state's
+    // precision; the error's maximum kept as a fraction en / ed (cross-multiplied
+    // comparisons, one division per thread)
+    T red_tq = 0, en = 0, ed = 1;
     if (x0 < nx && y < ny) {
         const int i = x0 + nx * (y + ny * z);
         const int sy = nx, sz = nx * ny;
@@ -263,9 +267,8 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
             const T pc = p.no_precession ? (T)0 : (T)1;
             kx[v] = gp * (pc * cx + al[v] * dx_); ky[v] = gp * (pc * cy + al[v] * dy_);
             kz[v] = gp * (pc * cz + al[v] * dz_);
-            if (!(isfinite(kx[v]) && isfinite(ky[v]) && isfinite(kz[v]))) red_nf = 1.0;
-            if (p.want_torque && Ms[v] != (T)0)
-                red_torque = fmax(red_torque, sqrt((double)cx * cx + (double)cy * cy + (double)cz * cz) / (double)Ms[v]);
+            if (!(isfinite(kx[v]) && isfinite(ky[v]) && isfinite(kz[v]))) red_nf = 1;
+            if (p.want_torque && Ms[v] != (T)0) red_tq = fmax(red_tq, sqrt(cx * cx + cy * cy + cz * cz) / Ms[v]);
             if (p.want_energy && Ms[v] != (T)0) {
                 const double f = -0.5 * kMu0 * (p.lvol ? p.lvol[z] : p.V) * (double)Ms[v];
                 red_e0 += f * ((double)mx[v] * hdxv + (double)my[v] * hdyv + (double)mz[v] * hdzv);
@@ -293,10 +296,10 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
             T snx[VEC], sny[VEC], snz[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) { snx[v] = p.ckT * kx[v]; sny[v] = p.ckT * ky[v]; snz[v] = p.ckT * kz[v]; }
-            double ex_[VEC], ey_[VEC], ez_[VEC];
+            T ex_[VEC], ey_[VEC], ez_[VEC];
             if (p.want_err) {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) { ex_[v] = p.eb_k * kx[v]; ey_[v] = p.eb_k * ky[v]; ez_[v] = p.eb_k * kz[v]; }
+                for (int v = 0; v < VEC; ++v) { ex_[v] = p.eb_kT * kx[v]; ey_[v] = p.eb_kT * ky[v]; ez_[v] = p.eb_kT * kz[v]; }
             }
             for (int q = 0; q < p.nk; ++q) {
                 const T* kq = p.kin[q];
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) { snx[v] += c * ax[v]; sny[v] += c * ay[v]; snz[v] += c * az[v]; }
                 if (p.want_err) {
-                    const double e = p.eb[q];
+                    const T e = p.ebT[q];
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) { ex_[v] += e * ax[v]; ey_[v] += e * ay[v]; ez_[v] += e * az[v]; }
                 }
@@ -321,13 +324,14 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
                     const T ux = p.err_on_next ? m0x[v] + p.dtT * snx[v] : mx[v];
                     const T uy = p.err_on_next ? m0y[v] + p.dtT * sny[v] : my[v];
                     const T uz = p.err_on_next ? m0z[v] + p.dtT * snz[v] : mz[v];
-                    const double scx = p.atol + p.rtol * fmax(fabs((double)m0x[v]), fabs((double)ux));
-                    const double scy = p.atol + p.rtol * fmax(fabs((double)m0y[v]), fabs((double)uy));
-                    const double scz = p.atol + p.rtol * fmax(fabs((double)m0z[v]), fabs((double)uz));
-                    const double r = fmax(fmax(fabs(p.dt * ex_[v]) / scx, fabs(p.dt * ey_[v]) / scy),
-                                          fabs(p.dt * ez_[v]) / scz);
-                    if (!isfinite(r)) red_nf = 1.0;
-                    red_err = fmax(red_err, r);
+                    const T scx = p.atolT + p.rtolT * fmax(fabs(m0x[v]), fabs(ux));
+                    const T scy = p.atolT + p.rtolT * fmax(fabs(m0y[v]), fabs(uy));
+                    const T scz = p.atolT + p.rtolT * fmax(fabs(m0z[v]), fabs(uz));
+                    const T nx = fabs(p.dtT * ex_[v]), ny = fabs(p.dtT * ey_[v]), nz = fabs(p.dtT * ez_[v]);
+                    if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) red_nf = 1;
+                    if (nx * ed > en * scx) { en = nx; ed = scx; }
+                    if (ny * ed > en * scy) { en = ny; ed = scy; }
+                    if (nz * ed > en * scz) { en = nz; ed = scz; }
                 }
             }
             if (p.next) {
@@ -351,27 +355,45 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks<T, DMI>()) sta
     }
     // ---- block reduction (all threads participate) ----
     if (p.partials) {
-        __shared__ double red[kStageThreads / 32][kNPart];
+        // energies: FP64 sums; torque, error and the non-finite flag: maxima in
+        // the state's precision, the error as a fraction divided once per block
+        constexpr int NW = kStageThreads / 32;
+        __shared__ double red[NW][kNPart];
+        __shared__ T redt[NW][3];
         const int tid = threadIdx.y * kBX + threadIdx.x;
         const int lane = tid & 31, wid = tid >> 5;
-        double vals[kNPart] = {red_torque, red_e0, red_e1, red_e2, red_e3, red_err, red_nf, red_e4};
-        vals[R_TORQUE] = warp_max(vals[R_TORQUE]);
-        vals[R_ERR] = warp_max(vals[R_ERR]);
-        vals[R_NONFINITE] = warp_max(vals[R_NONFINITE]);
+        double vals[kNPart] = {0.0, red_e0, red_e1, red_e2, red_e3, 0.0, 0.0, red_e4};
+        if (p.want_energy) {
 #pragma unroll
-        for (int q = R_EDEM; q <= R_EZEE; ++q) vals[q] = warp_sum(vals[q]);
-        vals[R_EDMI] = warp_sum(vals[R_EDMI]);
+            for (int q = R_EDEM; q <= R_EZEE; ++q) vals[q] = warp_sum(vals[q]);
+            vals[R_EDMI] = warp_sum(vals[R_EDMI]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T n2 = __shfl_down_sync(0xffffffffu, en, o), d2 = __shfl_down_sync(0xffffffffu, ed, o);
+            if (n2 * ed > en * d2) { en = n2; ed = d2; }
+            red_tq = fmax(red_tq, __shfl_down_sync(0xffffffffu, red_tq, o));
+        }
+        const bool nf = __any_sync(0xffffffffu, red_nf);
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < kNPart; ++q) red[wid][q] = vals[q];
+            red[wid][R_NONFINITE] = nf ? 1.0 : 0.0;
+            redt[wid][0] = red_tq; redt[wid][1] = en; redt[wid][2] = ed;
         }
         __syncthreads();
         if (tid < kNPart) {
             const int q = tid;
             double acc = red[0][q];
-            for (int w = 1; w < kStageThreads / 32; ++w) {
-                const double v = red[w][q];
-                acc = (q == R_TORQUE || q == R_ERR || q == R_NONFINITE) ? fmax(acc, v) : acc + v;
+            if (q == R_TORQUE || q == R_ERR) {
+                T t = redt[0][0], n = redt[0][1], d = redt[0][2];
+                for (int w = 1; w < NW; ++w) {
+                    t = fmax(t, redt[w][0]);
+                    if (redt[w][1] * d > n * redt[w][2]) { n = redt[w][1]; d = redt[w][2]; }
+                }
+                acc = q == R_TORQUE ? (double)t : (double)(n / d);
+            } else {
+                for (int w = 1; w < NW; ++w) acc = q == R_NONFINITE ? fmax(acc, red[w][q]) : acc + red[w][q];
             }
             const long b = ((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             p.partials[b * kNPart + q] = acc;
@@ -478,6 +500,10 @@ template <typename T> void stage_prepare(StageParams<T>& p) {
     p.ckT = (T)p.ck;
     p.dtT = (T)p.dt;
     p.acc_bT = (T)p.acc_b;
+    for (int q = 0; q < 7; ++q) p.ebT[q] = (T)p.eb[q];
+    p.eb_kT = (T)p.eb_k;
+    p.rtolT = (T)p.rtol;
+    p.atolT = (T)p.atol;
     // uniform-material constants, computed once in double
     p.cex_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 / (double)p.Ms) : (T)0;
     p.cani_u = p.Ms != (T)0 ? (T)(2.0 / kMu0 * (double)p.Ku / (double)p.Ms) : (T)0;
