@@ -183,6 +183,26 @@ template <int DIR, typename C> __device__ __forceinline__ void dft6(C (&a)[6]) {
     a[2] = cadd(e2, w2); a[5] = csub(e2, w2);
 }
 
+// DFT12 in place by the prime-factor (Good-Thomas) split 12 = 4 x 3, which
+// needs no twiddles: input n = (3 n1 + 4 n2) mod 12 enters DFT4 number n2 at
+// place n1, then DFT3 number k1 runs over n2, and its output k2 is X at
+// k = (9 k1 + 4 k2) mod 12 (k = k1 mod 4, k = k2 mod 3)
+template <int DIR, typename C> __device__ __forceinline__ void dft12(C* a) {
+    C t[4][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2)
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) t[n1][n2] = a[(3 * n1 + 4 * n2) % 12];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) dft4<DIR>(t[0][n2], t[1][n2], t[2][n2], t[3][n2]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft3<DIR>(t[k1][0], t[k1][1], t[k1][2]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) a[(9 * k1 + 4 * k2) % 12] = t[k1][k2];
+}
+
 // DFT7 in place, X_q = sum_r a_r exp(DIR 2 pi i r q / 7), from the pairs
 // p_k = a_k + a_{7-k}, m_k = a_k - a_{7-k} (k = 1, 2, 3):
 // X_q, X_{7-q} = a0 + sum_k p_k cos(2 pi k q / 7) +- DIR i sum_k m_k sin(2 pi k q / 7)

@@ -1389,6 +1389,8 @@ p3_layers_tma(DemagDims d, const __grid_constant__ CUtensorMap tmap, const __gri
 // shared-memory table instead of being derived in every transform
 // (141.5 -> 136.3 us on the bulk grid)
 constexpr bool kZTwTab = true;
+// the 96-point z line (8 x 12) on the two-factor engine
+constexpr bool kZTwo = true;
 // the radix-16 engine's plan for a z line: one radix-16 pass after the first, and its first radix
 template <int L> __host__ __device__ constexpr bool z_one_pass16() {
     if constexpr (is_pow2(L) && L >= 16) return FftLine16<float, L, -1, true>::NPASS == 2;
@@ -1546,6 +1548,152 @@ p3_z_tma(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_c
             for (int r = 0; r < NOUT; ++r) {
                 const int z = j + r * TPL;
                 if (z < nz) {
+                    col[z * zs] = vx[r];
+                    col[cstride + z * zs] = vy[r];
+                    col[2 * cstride + z * zs] = vz[r];
+                }
+            }
+        }
+    }
+}
+
+// TMA z pass on the two-factor engine (FP32; L = R1 R2, e.g. 96 = 8 x 12):
+// the tiles, loads, barriers and tensor product are those of p3_z_tma; each
+// transform makes one exchange through the scratch area instead of one per
+// radix pass, and the spectra stay in the forward's order (fr_index), which
+// the tensor product and the inverse take as they are.
+template <int R1, int R2> struct ZTwoTpl { static constexpr int value = 4; };
+template <int R1, int R2, int B>
+__global__ void __launch_bounds__(B * ZTwoTpl<R1, R2>::value, 4)
+p3_z_two(DemagDims d, const __grid_constant__ CUtensorMap s2_map, const __grid_constant__ CUtensorMap t_map,
+         float2* __restrict__ S2, int s2_bytes, int t_bytes) {
+    using C = float2;
+    constexpr int TPL = ZTwoTpl<R1, R2>::value;
+    using FF = FftTwo<float, R1, R2, TPL, -1, true>;
+    using FI = FftTwo<float, R1, R2, TPL, +1, false>;
+    constexpr int LZ = R1 * R2, NR = FF::NR;
+    constexpr int KZ2 = LZ / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smtma[];
+    C* cs = reinterpret_cast<C*>(smtma);                                        // [c][z][kx]
+    const float* ts = reinterpret_cast<const float*>(smtma + s2_bytes);         // [comp][kz'][kx]
+    C* scr = reinterpret_cast<C*>(smtma + s2_bytes + t_bytes);                  // [LZ][kx]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + s2_bytes + t_bytes + (size_t)LZ * B * sizeof(C));
+    __shared__ C tw[LZ];                                                        // W_L^m, forward sign
+    const int tid = threadIdx.x;
+    const int line = tid % B, j = tid / B;
+    const int nz = d.nz, LY = d.LY;
+    const int nkt = (d.KX + B - 1) / B;
+    const int ntiles = nkt * LY;
+    const uint32_t s2_tx = (uint32_t)(3 * nz * B * sizeof(C));
+    const uint32_t t_tx = (uint32_t)(6 * KZ2 * B * sizeof(float));
+    for (int e = tid; e < LZ; e += blockDim.x) tw[e] = twiddle5<float, -1>(e * (kTw5 / LZ));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);     // S2 columns
+        mbar_init(&bar[1], 1);     // tensor slice
+        fence_mbar_init();
+    }
+    __syncthreads();
+    grid_dep_wait();      // the previous pass's output is complete from here on
+    auto ky_of = [&](int kyo, int& p, int& side) {
+        p = (kyo + 1) >> 1;
+        side = (kyo > 0 && (kyo & 1) == 0) ? 1 : 0;
+        return side ? LY - p : p;
+    };
+    auto issue_s2 = [&](int t) {
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        const int ky = ky_of(kyo, p, side);
+        mbar_arrive_expect_tx(&bar[0], s2_tx);
+        tma_load_4d(smtma, &s2_map, &bar[0], kt * B, ky, 0, 0);
+    };
+    auto issue_t = [&](int t) {
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        ky_of(kyo, p, side);
+        mbar_arrive_expect_tx(&bar[1], t_tx);
+        tma_load_4d(smtma + s2_bytes, &t_map, &bar[1], kt * B, p, 0, 0);
+    };
+    const int t0 = blockIdx.x;
+    if (tid == 0 && t0 < ntiles) {
+        issue_s2(t0);
+        issue_t(t0);
+    }
+    int i = 0;
+    for (int t = t0; t < ntiles; t += gridDim.x, ++i) {
+        pdl_trigger_late(t + (int)gridDim.x >= ntiles);
+        const uint32_t par = i & 1;
+        const bool more = t + (int)gridDim.x < ntiles;
+        bool ok = mbar_wait_bounded(&bar[0], par);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                mbar_wait_bounded(&bar[0], par);                 // the late columns
+                mbar_wait_bounded(&bar[1], par);                 // this tile's tensor slice is in flight
+            }
+            return;
+        }
+        const int kt = t % nkt, kyo = t / nkt;
+        int p, side;
+        const int ky = ky_of(kyo, p, side);
+        C vx[NR], vy[NR], vz[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int z = FF::sp_index(j, r);
+            const bool live = FF::sp_half(r) && z < nz;
+            vx[r] = live ? cs[(0 * nz + z) * B + line] : mk<C>(0, 0);
+            vy[r] = live ? cs[(1 * nz + z) * B + line] : mk<C>(0, 0);
+            vz[r] = live ? cs[(2 * nz + z) * B + line] : mk<C>(0, 0);
+        }
+        __syncthreads();   // the columns are in registers: the buffer takes the next tile's
+        if (tid == 0 && more) {
+            fence_proxy_async_smem();
+            issue_s2(t + gridDim.x);
+        }
+        FF::run(vx, scr + line, B, j, tw);
+        FF::run(vy, scr + line, B, j, tw);
+        FF::run(vz, scr + line, B, j, tw);
+        ok = mbar_wait_bounded(&bar[1], par);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(d.err, kErrTmaTimeout);
+                mbar_wait_bounded(&bar[1], par);                  // the late slice
+                if (more) mbar_wait_bounded(&bar[0], par ^ 1u);   // the next tile's columns are in flight
+            }
+            return;
+        }
+        const float sy = side ? -1.f : 1.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int kz = FF::fr_index(j, r);
+            const int kzf = (2 * kz <= LZ) ? kz : LZ - kz;
+            const float sz = (2 * kz <= LZ) ? 1.f : -1.f;
+            const float txx = ts[(0 * KZ2 + kzf) * B + line];
+            const float txy = (d.yz_swap ? sz : sy) * ts[(1 * KZ2 + kzf) * B + line];
+            const float txz = (d.yz_swap ? sy : sz) * ts[(2 * KZ2 + kzf) * B + line];
+            const float tyy = ts[(3 * KZ2 + kzf) * B + line];
+            const float tyz = sy * sz * ts[(4 * KZ2 + kzf) * B + line];
+            const float tzz = ts[(5 * KZ2 + kzf) * B + line];
+            const C mx = vx[r], my = vy[r], mz = vz[r];
+            vx[r] = mk<C>(txx * mx.x + txy * my.x + txz * mz.x, txx * mx.y + txy * my.y + txz * mz.y);
+            vy[r] = mk<C>(txy * mx.x + tyy * my.x + tyz * mz.x, txy * mx.y + tyy * my.y + tyz * mz.y);
+            vz[r] = mk<C>(txz * mx.x + tyz * my.x + tzz * mz.x, txz * mx.y + tyz * my.y + tzz * mz.y);
+        }
+        __syncthreads();   // the slice has been read: the buffer takes the next tile's
+        if (tid == 0 && more) {
+            fence_proxy_async_smem();
+            issue_t(t + gridDim.x);
+        }
+        FI::run(vx, scr + line, B, j, tw);
+        FI::run(vy, scr + line, B, j, tw);
+        FI::run(vz, scr + line, B, j, tw);
+        const int kx = kt * B + line;
+        if (kx < d.KX) {
+            const long cstride = (long)nz * LY * d.KXS, zs = (long)LY * d.KXS;
+            C* col = S2 + (long)ky * d.KXS + kx;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int z = FI::sp_index(j, r);
+                if (FI::sp_half(r) && z < nz) {
                     col[z * zs] = vx[r];
                     col[cstride + z * zs] = vy[r];
                     col[2 * cstride + z * zs] = vz[r];
@@ -1806,6 +1954,40 @@ static bool launch_p3_tma(const DemagDims& d, float2* S2, const float* tens, cud
     return true;
 }
 
+// factors of the z lines that run the two-factor TMA z pass (0: none)
+template <int L> constexpr int z_two_r1() { return L == 96 ? 8 : 0; }
+template <int L> constexpr int z_two_r2() { return L == 96 ? 12 : 0; }
+
+// TMA z pass on the two-factor engine: false if it cannot be used
+template <int L>
+static bool launch_p3_two(const DemagDims& d, float2* S2, const float* tens, cudaStream_t st) {
+    constexpr int B = 16, R1 = z_two_r1<L>(), R2 = z_two_r2<L>();
+    static_assert(R1 * R2 == L, "two-factor z line");
+    if (!d.err || (d.KXS * 8) % 16 != 0 || (d.KXS * 4) % 16 != 0 || d.nz > L / 2) return false;
+    if ((reinterpret_cast<uintptr_t>(S2) & 15) != 0 || (reinterpret_cast<uintptr_t>(tens) & 15) != 0) return false;
+    const int KY2 = d.LY / 2 + 1, KZ2 = L / 2 + 1;
+    CUtensorMap s2m, tm;
+    const cuuint64_t sd[4] = {(cuuint64_t)d.KX, (cuuint64_t)d.LY, (cuuint64_t)d.nz, 3};
+    const cuuint64_t ss[3] = {(cuuint64_t)d.KXS * 8, (cuuint64_t)d.LY * d.KXS * 8, (cuuint64_t)d.nz * d.LY * d.KXS * 8};
+    const cuuint32_t sb[4] = {(cuuint32_t)B, 1, (cuuint32_t)d.nz, 3};
+    const cuuint64_t td[4] = {(cuuint64_t)d.KX, (cuuint64_t)KY2, (cuuint64_t)KZ2, 6};
+    const cuuint64_t ts[3] = {(cuuint64_t)d.KXS * 4, (cuuint64_t)KY2 * d.KXS * 4, (cuuint64_t)KZ2 * KY2 * d.KXS * 4};
+    const cuuint32_t tb[4] = {(cuuint32_t)B, 1, (cuuint32_t)KZ2, 6};
+    if (!encode_4d(&s2m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, S2, sd, ss, sb)) return false;
+    if (!encode_4d(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tens, td, ts, tb)) return false;
+    const int s2_bytes = (int)((3 * (size_t)d.nz * B * sizeof(float2) + 127) / 128 * 128);
+    const int t_bytes = (int)((6 * (size_t)KZ2 * B * sizeof(float) + 127) / 128 * 128);
+    const int nkt = (d.KX + B - 1) / B;
+    const size_t sm = (size_t)s2_bytes + t_bytes + (size_t)L * B * sizeof(float2) + 16;
+    if (sm > 200 * 1024) return false;
+    auto k = p3_z_two<R1, R2, B>;
+    set_smem(k, sm);
+    const int threads = B * ZTwoTpl<R1, R2>::value;
+    const int grid = persistent_grid(k, threads, sm, nkt * d.LY);
+    launch_pdl(k, grid, threads, sm, st, d, s2m, tm, S2, s2_bytes, t_bytes);
+    return true;
+}
+
 // widest multiple of 8 elements <= 256 that covers n in the fewest boxes
 static int box_width(int n, int* nboxes) {
     const int nb = (n + 255) / 256;
@@ -1881,6 +2063,9 @@ template <typename T, int L> static void launch_p3(const DemagDims& d, typename 
     dim3 grid((d.KX + B - 1) / B, (kyi + G - 1) / G, d.nb);
     // the register-resident variant holds 3 NR values per thread: up to 20
     if constexpr (sizeof(T) == 4 && L <= 256 && Fft<T, L, -1, (L > 1)>::NR <= 20) {
+        if constexpr (z_two_r1<L>() > 0) {
+            if (kZTwo && d.nb == 1 && launch_p3_two<L>(d, S2, tens, st)) return;
+        }
         if constexpr (tma_len<L>()) {
             if (d.nb == 1 && launch_p3_tma<L>(d, S2, tens, st)) return;
         }

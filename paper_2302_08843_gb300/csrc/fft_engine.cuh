@@ -354,6 +354,92 @@ struct FftMixed {
     }
 };
 
+// ------------------------------------------------------------------------
+// Two-factor engine L = R1 R2 (Cooley-Tukey with one shared-memory exchange
+// per transform), TPL threads per line, TPL dividing R1 and R2.
+//   forward: x at n = R2 n1 + n2; DFT_R1 over n1 for each n2, times
+//            W_L^(n2 k1), exchange, DFT_R2 over n2 for each k1 -> X at k1 + R1 k2
+//   inverse: X at k1 + R1 k2; DFT_R2 over k2 for each k1, times W_L^(-na k1),
+//            exchange, DFT_R1 over k1 for each na -> x at na + R2 nb
+// Register r of thread j holds the spatial element sp_index(j, r) (the
+// forward's input, the inverse's output) or the spectral element
+// fr_index(j, r) (the forward's output, the inverse's input): the spectrum
+// stays in the forward's order, so a pointwise product between the two
+// transforms needs no exchange.  Spatial place n < L/2 is register r with
+// r mod R1 < R1/2 (the zero-padded input half, the kept output half).  The
+// twiddles W_L^m (m < L, forward sign) come from a table tw.
+template <typename T, int R1, int R2, int TPL, int DIR, bool ZIN>
+struct FftTwo {
+    using C = typename Cplx<T>::type;
+    static_assert(R1 % TPL == 0 && R2 % TPL == 0, "threads per line must divide both factors");
+    static_assert(R1 % 2 == 0, "the zero-padded half must be whole DFT_R1 inputs");
+    static constexpr int L = R1 * R2, NR = L / TPL, NA = R2 / TPL, NB = R1 / TPL;
+    static __device__ __forceinline__ int sp_index(int j, int r) { return j + (r / R1) * TPL + R2 * (r % R1); }
+    static __device__ __forceinline__ int fr_index(int j, int r) { return j + (r / R2) * TPL + R1 * (r % R2); }
+    static __host__ __device__ constexpr bool sp_half(int r) { return r % R1 < R1 / 2; }
+
+    template <int R, bool HALF> static __device__ __forceinline__ void dftr(C* a) {
+        if constexpr (R == 8) {
+            if constexpr (HALF) dft8_half<DIR>(a); else dft8<DIR>(a);
+        } else if constexpr (R == 12) {
+            dft12<DIR>(a);
+        } else if constexpr (R == 4) {
+            dft4<DIR>(a[0], a[1], a[2], a[3]);
+        } else {
+            static_assert(R == 4 || R == 8 || R == 12, "factor without a register DFT");
+        }
+    }
+    static __device__ __forceinline__ C tws(const C* tw, int m) {
+        const C w = tw[m];
+        return DIR < 0 ? w : mk<C>(w.x, -w.y);
+    }
+    // s: the line's exchange scratch (element e at s[e LS]); every thread of
+    // the block calls run (it synchronises the block)
+    static __device__ __forceinline__ void run(C (&v)[NR], C* s, int LS, int j, const C* tw) {
+        if constexpr (DIR < 0) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                dftr<R1, ZIN>(v + a * R1);
+                const int n2 = j + a * TPL;
+#pragma unroll
+                for (int k1 = 1; k1 < R1; ++k1) v[a * R1 + k1] = cmul(v[a * R1 + k1], tws(tw, n2 * k1));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) s[(k1 * R2 + j + a * TPL) * LS] = v[a * R1 + k1];
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2) v[b * R2 + n2] = s[((j + b * TPL) * R2 + n2) * LS];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) dftr<R2, false>(v + b * R2);
+        } else {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                dftr<R2, false>(v + b * R2);
+                const int k1 = j + b * TPL;
+#pragma unroll
+                for (int na = 1; na < R2; ++na) v[b * R2 + na] = cmul(v[b * R2 + na], tws(tw, na * k1));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int na = 0; na < R2; ++na) s[((j + b * TPL) * R2 + na) * LS] = v[b * R2 + na];
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) v[a * R1 + k1] = s[(k1 * R2 + j + a * TPL) * LS];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) dftr<R1, false>(v + a * R1);
+        }
+    }
+};
+
 // engine choice: the mixed-radix engine for the r 2^a lengths, radix 16 for
 // FP32 power-of-two lines of 16+ points, radix 8 otherwise
 template <typename T, int L, int DIR, bool ZIN>

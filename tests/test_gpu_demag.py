@@ -33,6 +33,10 @@ GRIDS = [
     ((12, 150, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 300 (runtime plan)
     ((12, 190, 3), (2e-9, 2e-9, 3e-9)),         # y padded to 384
     ((10, 8, 48), (2e-9, 2e-9, 2e-9)),          # z padded to 96
+    # the 96-point z line on the two-factor engine (8 x 12): odd and even nz,
+    # several kx tiles with a ragged last tile
+    ((40, 8, 47), (2e-9, 2.5e-9, 2e-9)),        # z 96, 3 tiles of 16 kx
+    ((64, 12, 46), (2e-9, 2e-9, 3e-9)),         # z 96, 5 tiles (last one column)
     ((512, 3, 1), (2e-9, 2e-9, 2e-9)),          # x padded to 1024
     ((1024, 2, 1), (2e-9, 2e-9, 2e-9)),         # x padded to 2048
     # every mixed-radix length r 2^a (r = 3, 7, 25) on at least one axis
