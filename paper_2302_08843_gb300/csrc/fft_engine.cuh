@@ -307,8 +307,13 @@ struct FftMixed {
     static __device__ __forceinline__ int at(int e, int LS) { return e * LS; }   // shared-memory place of element e
     static __device__ void tw_build(C*, int, int) {}
 
+    // Pass P (NS = product of the earlier radices).  The first pass takes its
+    // butterflies' inputs from the registers (element b + q L/R of butterfly b
+    // = j + t TPL is register t + q NB of the same thread) and the last pass
+    // leaves its outputs there (its autosorted places are b + q L/R again), so
+    // a transform makes NP - 1 shared-memory exchanges.
     template <int P, int NS>
-    static __device__ __forceinline__ void pass(C* s, int LS, int j) {
+    static __device__ __forceinline__ void pass(C* v, C* s, int LS, int j) {
         constexpr int R = m5_radix(L, P, ALT);
         constexpr int NB = L / (R * TPL);    // butterflies per thread
         C a[NB][R];
@@ -317,7 +322,7 @@ struct FftMixed {
             const int b = j + t * TPL;
             const int k = b % NS;
 #pragma unroll
-            for (int q = 0; q < R; ++q) a[t][q] = s[(b + q * (L / R)) * LS];
+            for (int q = 0; q < R; ++q) a[t][q] = P == 0 ? v[t + q * NB] : s[(b + q * (L / R)) * LS];
             if (NS > 1) {
 #pragma unroll
                 for (int q = 1; q < R; ++q) a[t][q] = cmul(a[t][q], twiddle5<T, DIR>(q * k * (kTw5 / (NS * R))));
@@ -330,27 +335,28 @@ struct FftMixed {
             else if constexpr (R == 3) dft3<DIR>(a[t][0], a[t][1], a[t][2]);
             else dft2<DIR>(a[t][0], a[t][1]);
         }
-        __syncthreads();
+        if constexpr (P + 1 == NP) {
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-            const int b = j + t * TPL;
-            const int k = b % NS;
-            const int base = (b - k) * R + k;
+            for (int t = 0; t < NB; ++t)
 #pragma unroll
-            for (int q = 0; q < R; ++q) s[(base + q * NS) * LS] = a[t][q];
+                for (int q = 0; q < R; ++q) v[t + q * NB] = a[t][q];
+        } else {
+            __syncthreads();   // every read of the scratch (this pass's, or an earlier user's) is done
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const int b = j + t * TPL;
+                const int k = b % NS;
+                const int base = (b - k) * R + k;
+#pragma unroll
+                for (int q = 0; q < R; ++q) s[(base + q * NS) * LS] = a[t][q];
+            }
+            __syncthreads();
+            pass<P + 1, NS * R>(v, s, LS, j);
         }
-        __syncthreads();
-        if constexpr (P + 1 < NP) pass<P + 1, NS * R>(s, LS, j);
     }
 
     static __device__ __forceinline__ void run(C* v, C* s, int LS, int j, const C* = nullptr) {
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < NR; ++r) s[(j + r * TPL) * LS] = v[r];
-        __syncthreads();
-        pass<0, 1>(s, LS, j);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = s[(j + r * TPL) * LS];
+        pass<0, 1>(v, s, LS, j);
     }
 };
 
