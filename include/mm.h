@@ -212,7 +212,8 @@ mm_status mm_llg_step_adjoint(mm_state* s, const void* m_n, const void* lambda_n
 
 /* ---- Batched relaxation (served requests) ----
  * A batch holds up to `capacity` grids of one shape (nx, ny, nz, cell size),
- * each a "slot" with its own uniform Ms, A, alpha, magnetisation and
+ * each a "slot" with its own uniform Ms, A, alpha, optional uniform DMI and
+ * precession switch (mm_batch_set_slot_terms), magnetisation and
  * Dormand-Prince step, relaxed as in mm_relax (Sec. 3: integrate with the
  * material's damping until max |m x h| / Ms < tol).  The demag tensor
  * spectrum is built once per batch (the size bucket's plan) and shared by
@@ -236,6 +237,16 @@ void mm_batch_destroy(mm_batch* b);
  * MM_EINVAL if the slot is out of range or busy. */
 mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double alpha, const void* m0,
                             int on_device, double dt0);
+
+/* Field terms of a freshly loaded slot (after mm_batch_set_slot, before the
+ * next mm_batch_begin): the DMI term of Sec. 4.3 with `dmi_kind`
+ * (mm_dmi_kind) and a uniform D in J/m^2, as mm_set_dmi defines it (D = 0
+ * or MM_DMI_NONE: no DMI), and the precession switch of Sec. 3 (0: the m x h
+ * summand is left out, as mm_set_llg_options does).  mm_batch_set_slot
+ * resets both (no DMI, precession on).  Synchronises the batch's stream.
+ * MM_EINVAL for a slot that is not freshly loaded, a bad kind or a
+ * non-finite D. */
+mm_status mm_batch_set_slot_terms(mm_batch* b, int slot, int dmi_kind, double D, int precession);
 
 /* Free a slot (any state); its next request may be loaded at once. */
 mm_status mm_batch_clear_slot(mm_batch* b, int slot);

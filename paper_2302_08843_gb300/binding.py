@@ -26,6 +26,7 @@ EXPORTS = ("mm_state_create", "mm_state_destroy", "mm_set_material", "mm_set_m",
            "mm_relax", "mm_demag_tensor_host", "mm_demag_spectrum_host", "mm_state_info", "mm_profile_enable",
            "mm_profile_read", "mm_last_error", "mm_version", "mm_demag_noalloc", "mm_llg_step_adjoint",
            "mm_batch_footprint", "mm_batch_create", "mm_batch_destroy", "mm_batch_set_slot", "mm_batch_clear_slot",
+           "mm_batch_set_slot_terms",
            "mm_batch_begin", "mm_batch_query", "mm_batch_end", "mm_batch_get_m",
            "mm_selftest_wait_timeout", "mm_set_llg_options", "mm_set_dmi", "mm_fft_extent",
            "mm_set_layers", "mm_layers_spectrum_host", "mm_probe_fp64_fma", "mm_llg_rhs")
@@ -92,6 +93,7 @@ def lib():
         "mm_batch_create": (i, [ctypes.POINTER(mm_grid), i, i, i, vp, ctypes.POINTER(vp)]),
         "mm_batch_destroy": (None, [vp]),
         "mm_batch_set_slot": (i, [vp, i, d, d, d, vp, i, d]),
+        "mm_batch_set_slot_terms": (i, [vp, i, i, d, i]),
         "mm_batch_clear_slot": (i, [vp, i]),
         "mm_batch_begin": (i, [vp, i, d, d, i]),
         "mm_batch_query": (i, [vp, vp]),
@@ -444,6 +446,12 @@ class Batch:
             m0 = np.ascontiguousarray(m0, dtype=self.npdtype)
         p, dev = _ptr(m0)
         check(lib().mm_batch_set_slot(self.h, int(slot), float(Ms), float(A), float(alpha), p, dev, float(dt0)))
+
+    def set_slot_terms(self, slot, dmi=None, D=0.0, precession=True):
+        """mm_batch_set_slot_terms: DMI kind ("interface", "bulk", "d2d" or None)
+        with a uniform D, and the precession switch, for a freshly loaded slot."""
+        check(lib().mm_batch_set_slot_terms(self.h, int(slot), State.DMI_KINDS[dmi], float(D),
+                                            1 if precession else 0))
 
     def clear_slot(self, slot):
         check(lib().mm_batch_clear_slot(self.h, int(slot)))

@@ -7,6 +7,13 @@
 
 namespace mm {
 
+// out += e x w
+template <typename T> __device__ __forceinline__ void bcross_add(const T* e, T wx, T wy, T wz, T& ox, T& oy, T& oz) {
+    ox += e[1] * wz - e[2] * wy;
+    oy += e[2] * wx - e[0] * wz;
+    oz += e[0] * wy - e[1] * wx;
+}
+
 // one thread per cell, grid (ceil(N/256), nb); a masked-off grid does nothing
 template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(BatchStageParams<T> p) {
     const int b = blockIdx.y;
@@ -41,6 +48,24 @@ template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(
             MM_BLINK(z > 0, -p.nx * p.ny, p.idz2)
             MM_BLINK(z < p.nz - 1, p.nx * p.ny, p.idz2)
 #undef MM_BLINK
+            // DMI (Sec. 4.3), uniform D: sum over the axes of e_a x D (m_{i+a} - m_{i-a}) / (2 d_a),
+            // a neighbour outside the grid left out; it enters h with the exchange sum's 2 / (mu0 Ms)
+            const int kind = p.dmi_kind[b];
+            if (kind) {
+                const T* e = p.dmi_e[kind];
+#define MM_BDMI(LO, HI, OFF, EA, I2D)                                                 \
+                {                                                                     \
+                    T wx = 0, wy = 0, wz = 0;                                         \
+                    if (HI) { const int k = i + (OFF); wx += m[k]; wy += m[N + k]; wz += m[2 * N + k]; } \
+                    if (LO) { const int k = i - (OFF); wx -= m[k]; wy -= m[N + k]; wz -= m[2 * N + k]; } \
+                    const T c = p.D[b] * (I2D);                                       \
+                    bcross_add(EA, c * wx, c * wy, c * wz, sx, sy, sz);               \
+                }
+                MM_BDMI(x > 0, x < p.nx - 1, 1, e, p.i2dx)
+                MM_BDMI(y > 0, y < p.ny - 1, p.nx, e + 3, p.i2dy)
+                MM_BDMI(z > 0, z < p.nz - 1, p.nx * p.ny, e + 6, p.i2dz)
+#undef MM_BDMI
+            }
             const T cex = (T)(2.0 / kMu0) / Ms;
             const T* hd = p.hd + off;
             hx = hd[i] + cex * sx + p.hx0;
@@ -50,7 +75,8 @@ template <typename T> __global__ void __launch_bounds__(256) batch_stage_kernel(
         const T gp = (T)(-kGamma) / ((T)1 + al * al);
         cx = my * hz - mz * hy; cy = mz * hx - mx * hz; cz = mx * hy - my * hx;
         const T dx_ = my * cz - mz * cy, dy_ = mz * cx - mx * cz, dz_ = mx * cy - my * cx;
-        const T kx = gp * (cx + al * dx_), ky = gp * (cy + al * dy_), kz = gp * (cz + al * dz_);
+        const T pcf = p.pc[b];
+        const T kx = gp * (pcf * cx + al * dx_), ky = gp * (pcf * cy + al * dy_), kz = gp * (pcf * cz + al * dz_);
         if (!(isfinite(kx) && isfinite(ky) && isfinite(kz))) nf = 1;
         if (p.want_torque && Ms != (T)0) tq2 = cx * cx + cy * cy + cz * cz;
         if (p.k_out) { T* ko = p.k_out + off; ko[i] = kx; ko[N + i] = ky; ko[2 * N + i] = kz; }

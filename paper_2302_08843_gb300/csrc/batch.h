@@ -11,6 +11,13 @@ template <typename T> struct BatchStageParams {
     const T* Ms;              // [nb] per-grid material (device)
     const T* A;
     const T* alpha;
+    // per grid (Sec. 4.3, Sec. 3): DMI kind (0 none, 1 interface, 2 bulk, 3 D2d)
+    // with a uniform D, and the precession factor (1, or 0 without the m x h term)
+    const int* dmi_kind;
+    const T* D;
+    const T* pc;
+    T dmi_e[4][9];            // DMI vectors e_x, e_y, e_z of each kind
+    T i2dx, i2dy, i2dz;       // 1 / (2 d) per axis
     const double* dt;         // [nb] per-grid step
     const int* mask;          // [nb] grids this launch works on
     T hx0, hy0, hz0;          // uniform external field

@@ -327,9 +327,15 @@ template <int LX, int LS> __host__ __device__ constexpr int k5_work_elems() {
 }
 // the fused kernel's engines: radix-16 with the work-area skew for powers of
 // two, the shared-memory mixed-radix engine for the compiled r 2^a lengths
+// the mixed-radix lengths take the shorter radix plans (384 = 6 8 8: two
+// exchanges per transform, 24 values per thread) with six rows of y per tile
+// (192x192x48: 90.9 us with the radix-4 plan and two rows, 69.8 us so)
+#ifndef MM_K5_ALT
+#define MM_K5_ALT 1
+#endif
 template <int LX, int DIR, bool ZIN> struct K5Eng {
     using type = typename std::conditional<is_pow2(LX), FftLine16<float, (LX < 16 ? 16 : LX), DIR, ZIN, kK5Skew>,
-                                           FftMixed<float, LX, DIR, ZIN, false>>::type;
+                                           FftMixed<float, LX, DIR, ZIN, (MM_K5_ALT != 0)>>::type;
 };
 
 // link A of two cells (harmonic mean; zero if both are zero) and, across
@@ -2111,12 +2117,27 @@ template <typename T, int L> static void launch_x_inv(const DemagDims& d, const 
 // fused K5 launcher (see k5_fused): false if the shape or material does not qualify
 // k5_fused configuration: TMA slots, work-area row padding, resident CTAs per SM
 constexpr int kK5Rows = 2, kK5Slots = 1, kK5Pad = 0, kK5MinBlocks = 8;
-// resident CTAs asked of the register allocator: 8 for the radix-16 engine,
-// 4 for the mixed-radix one (its 12-28 values per thread would spill at 8)
-template <int L> constexpr int k5_minb() { return is_pow2(L) ? kK5MinBlocks : 4; }
+#ifndef MM_K5_MIXED_MINB
+#define MM_K5_MIXED_MINB 4
+#endif
+#ifndef MM_K5_MIXED_ROWS
+#define MM_K5_MIXED_ROWS 6
+#endif
+// rows of y per tile (the mixed lines above 448 points keep two: their
+// 32-thread lines would not fit six rows without spills)
+template <int L> constexpr int k5_rows() { return is_pow2(L) ? kK5Rows : (L <= 448 ? MM_K5_MIXED_ROWS : 2); }
+template <int L> constexpr int k5_threads() { return (3 * k5_rows<L>() / 2) * K5Eng<L, +1, false>::type::TPL; }
+// resident CTAs asked of the register allocator, capped so that a thread keeps
+// at least 85 (radix-16) or 113 (mixed-radix) registers: the long lines' larger
+// CTAs would spill otherwise (1024-point lines spilled at eight CTAs)
+template <int L> constexpr int k5_minb() {
+    return is_pow2(L) ? (768 / k5_threads<L>() < 1 ? 1 : (768 / k5_threads<L>() > kK5MinBlocks ? kK5MinBlocks : 768 / k5_threads<L>()))
+                      : (576 / k5_threads<L>() < 1 ? 1
+                         : (576 / k5_threads<L>() > MM_K5_MIXED_MINB ? MM_K5_MIXED_MINB : 576 / k5_threads<L>()));
+}
 
 template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const StageParams<float>& p, cudaStream_t st) {
-    constexpr int TY = kK5Rows;
+    constexpr int TY = k5_rows<L>();
     if constexpr (L < 16 || !(is_pow2(L) || kTw5 % L == 0)) {
         return false;
     } else {

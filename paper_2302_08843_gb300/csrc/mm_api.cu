@@ -267,6 +267,12 @@ void zeeman_at(const mm_state* s, double t, double h[3]) {
     }
 }
 
+// DMI vectors e_x, e_y, e_z of the paper's table per mm_dmi_kind (e_{-k} = -e_k; Sec. 4.3)
+const double kDmiVectors[4][9] = {{0, 0, 0, 0, 0, 0, 0, 0, 0},
+                                  {0, 1, 0, -1, 0, 0, 0, 0, 0},     // interface
+                                  {1, 0, 0, 0, 1, 0, 0, 0, 1},      // bulk
+                                  {-1, 0, 0, 0, 1, 0, 0, 0, 0}};    // D2d
+
 template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, const void* m, double t) {
     std::memset(&p, 0, sizeof(p));
     p.nx = s->g.nx; p.ny = s->g.ny; p.nz = s->g.nz;
@@ -295,15 +301,10 @@ template <typename T> void fill_common(const mm_state* s, StageParams<T>& p, con
         p.lvol = s->lay_v;
     }
     if (s->dmi_kind != MM_DMI_NONE && (s->D != 0.0 || s->D_cell)) {
-        // DMI vectors e_x, e_y, e_z of the paper's table (e_{-k} = -e_k)
-        static const double vecs[4][9] = {{0, 0, 0, 0, 0, 0, 0, 0, 0},
-                                          {0, 1, 0, -1, 0, 0, 0, 0, 0},     // interface
-                                          {1, 0, 0, 0, 1, 0, 0, 0, 1},      // bulk
-                                          {-1, 0, 0, 0, 1, 0, 0, 0, 0}};    // D2d
         p.dmi = 1;
         p.D = (T)s->D;
         p.D_cell = (const T*)s->D_cell;
-        for (int q = 0; q < 9; ++q) p.dmi_e[q] = (T)vecs[s->dmi_kind][q];
+        for (int q = 0; q < 9; ++q) p.dmi_e[q] = (T)kDmiVectors[s->dmi_kind][q];
     }
 }
 
@@ -801,6 +802,11 @@ struct mm_batch {
     void* Ms_d = nullptr;
     void* A_d = nullptr;
     void* alpha_d = nullptr;
+    // per-slot field terms (mm_batch_set_slot_terms): DMI D, precession factor, DMI kind
+    void* D_d = nullptr;
+    void* pc_d = nullptr;
+    int* kind_d = nullptr;
+    std::vector<char> unstarted;   // loaded and not yet in an mm_batch_begin
     // per-slot controller state, on the device: status, steps, fresh, dt, t, torque
     int* ctl_i = nullptr;        // [3][cap] ints
     double* ctl_d = nullptr;     // [3][cap] doubles
@@ -843,7 +849,7 @@ size_t batch_bytes(const mm_grid* g, mm_precision prec, int cap, int* LXo, int* 
     if (LY > 1) bytes += (size_t)cap * 3 * csz * g->nz * LY * KXS;              // S2
     bytes += 6 * rsz * (size_t)(LZ / 2 + 1) * (LY / 2 + 1) * KXS;               // tensor
     const size_t nblk = (N + 255) / 256;
-    bytes += (size_t)cap * (2 * nblk * 3 * 8 + 3 * rsz + 3 * 4 + 3 * 8 + 2 * 4 + 4 + 2 * 3 * 8);
+    bytes += (size_t)cap * (2 * nblk * 3 * 8 + 5 * rsz + 4 + 3 * 4 + 3 * 8 + 2 * 4 + 4 + 2 * 3 * 8);
     if (LXo) { *LXo = LX; *LYo = LY; *LZo = LZ; *KXSo = KXS; }
     return bytes;
 }
@@ -858,6 +864,10 @@ template <typename T> mm_status batch_stage(mm_batch* b, const void* m, const vo
     p.idy2 = (T)(1.0 / (b->g.dy * b->g.dy));
     p.idz2 = (T)(1.0 / (b->g.dz * b->g.dz));
     p.Ms = (const T*)b->Ms_d; p.A = (const T*)b->A_d; p.alpha = (const T*)b->alpha_d;
+    p.dmi_kind = b->kind_d; p.D = (const T*)b->D_d; p.pc = (const T*)b->pc_d;
+    for (int k = 0; k < 4; ++k)
+        for (int q = 0; q < 9; ++q) p.dmi_e[k][q] = (T)kDmiVectors[k][q];
+    p.i2dx = (T)(0.5 / b->g.dx); p.i2dy = (T)(0.5 / b->g.dy); p.i2dz = (T)(0.5 / b->g.dz);
     p.dt = b->dt_d();
     p.mask = mask;
     p.m = (const T*)m; p.hd = (const T*)b->hd; p.mn = (const T*)mn;
@@ -1366,7 +1376,7 @@ void mm_batch_destroy(mm_batch* b) {
     cudaStreamSynchronize(b->st);
     batch_drop_graphs(b);
     void** bufs[] = {&b->m, &b->Y[0], &b->Y[1], &b->hd, &b->S1, &b->S2, &b->tens, &b->Ms_d, &b->A_d, &b->alpha_d,
-                     reinterpret_cast<void**>(&b->ctl_i), reinterpret_cast<void**>(&b->ctl_d),
+                     &b->D_d, &b->pc_d, reinterpret_cast<void**>(&b->kind_d), reinterpret_cast<void**>(&b->ctl_i), reinterpret_cast<void**>(&b->ctl_d),
                      reinterpret_cast<void**>(&b->mask_d), reinterpret_cast<void**>(&b->acc_d),
                      reinterpret_cast<void**>(&b->partials), reinterpret_cast<void**>(&b->scal_d)};
     for (void** q : bufs) dev_free(*q);
@@ -1418,6 +1428,9 @@ mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capac
     if ((st = dev_alloc(&b->Ms_d, b->rsz * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(&b->A_d, b->rsz * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(&b->alpha_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->D_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(&b->pc_d, b->rsz * capacity)) != MM_OK) return bail(st);
+    if ((st = dev_alloc(reinterpret_cast<void**>(&b->kind_d), sizeof(int) * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&b->ctl_i), sizeof(int) * 3 * capacity)) != MM_OK) return bail(st);
     if ((st = dev_alloc(reinterpret_cast<void**>(&b->ctl_d), sizeof(double) * 3 * capacity)) != MM_OK)
         return bail(st);
@@ -1452,11 +1465,15 @@ mm_status mm_batch_create(const mm_grid* grid, mm_precision precision, int capac
     if (e == cudaSuccess && s2) e = cudaMemsetAsync(b->S2, 0, s2, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->m, 0, v3, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->Ms_d, 0, b->rsz * capacity, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->D_d, 0, b->rsz * capacity, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->pc_d, 0, b->rsz * capacity, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->kind_d, 0, sizeof(int) * capacity, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl_i, 0, sizeof(int) * 3 * capacity, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl_d, 0, sizeof(double) * 3 * capacity, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return bail(fail(MM_ECUDA, "batch set-up: %s", cudaGetErrorString(e)));
     b->status.assign(capacity, 0);
+    b->unstarted.assign(capacity, 0);
     *out = b;
     return MM_OK;
 }
@@ -1472,9 +1489,11 @@ mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double a
     const size_t v = 3 * b->rsz * (size_t)b->N;
     MM_CUDA(cudaMemcpyAsync(static_cast<char*>(b->m) + slot * v, m0, v,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->st));
-    const double mat[3] = {Ms, A, alpha};
-    void* dst[3] = {b->Ms_d, b->A_d, b->alpha_d};
-    for (int q = 0; q < 3; ++q) {
+    // the slot's material; no DMI and the precession term on until mm_batch_set_slot_terms
+    const double mat[5] = {Ms, A, alpha, 0.0, 1.0};
+    void* dst[5] = {b->Ms_d, b->A_d, b->alpha_d, b->D_d, b->pc_d};
+    MM_CUDA(cudaMemsetAsync(b->kind_d + slot, 0, sizeof(int), b->st));
+    for (int q = 0; q < 5; ++q) {
         if (b->prec == MM_FP64) {
             MM_CUDA(cudaMemcpyAsync(static_cast<double*>(dst[q]) + slot, &mat[q], 8, cudaMemcpyHostToDevice, b->st));
         } else {
@@ -1492,7 +1511,32 @@ mm_status mm_batch_set_slot(mm_batch* b, int slot, double Ms, double A, double a
     MM_CUDA(cudaMemcpyAsync(b->torque_d() + slot, &dz, sizeof(double), cudaMemcpyHostToDevice, b->st));
     MM_CUDA(cudaStreamSynchronize(b->st));   // the host values above are stack copies
     b->status[slot] = 1;
+    b->unstarted[slot] = 1;
     b->fresh_any = true;
+    return MM_OK;
+}
+
+mm_status mm_batch_set_slot_terms(mm_batch* b, int slot, int dmi_kind, double D, int precession) {
+    if (!b) return fail(MM_EINVAL, "null batch");
+    if (slot < 0 || slot >= b->cap) return fail(MM_EINVAL, "slot %d out of range", slot);
+    if (b->pending) return fail(MM_EINVAL, "attempts are in flight: call mm_batch_end first");
+    if (!b->unstarted[slot]) return fail(MM_EINVAL, "slot %d is not freshly loaded", slot);
+    if (dmi_kind < MM_DMI_NONE || dmi_kind > MM_DMI_D2D || !std::isfinite(D))
+        return fail(MM_EINVAL, "bad DMI kind or strength");
+    MM_CUDA(cudaSetDevice(b->device));
+    const int kind = D != 0.0 ? dmi_kind : MM_DMI_NONE;
+    const double v[2] = {D, precession ? 1.0 : 0.0};
+    void* dst[2] = {b->D_d, b->pc_d};
+    for (int q = 0; q < 2; ++q) {
+        if (b->prec == MM_FP64) {
+            MM_CUDA(cudaMemcpyAsync(static_cast<double*>(dst[q]) + slot, &v[q], 8, cudaMemcpyHostToDevice, b->st));
+        } else {
+            const float f = (float)v[q];
+            MM_CUDA(cudaMemcpyAsync(static_cast<float*>(dst[q]) + slot, &f, 4, cudaMemcpyHostToDevice, b->st));
+        }
+    }
+    MM_CUDA(cudaMemcpyAsync(b->kind_d + slot, &kind, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    MM_CUDA(cudaStreamSynchronize(b->st));   // the host values above are stack copies
     return MM_OK;
 }
 
@@ -1506,6 +1550,7 @@ mm_status mm_batch_clear_slot(mm_batch* b, int slot) {
     MM_CUDA(cudaMemcpyAsync(b->fresh_d() + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, b->st));
     MM_CUDA(cudaStreamSynchronize(b->st));
     b->status[slot] = 0;
+    b->unstarted[slot] = 0;
     return MM_OK;
 }
 
@@ -1515,6 +1560,7 @@ mm_status mm_batch_begin(mm_batch* b, int attempts, double rtol, double tol, int
     if (!(rtol > 0) || !(tol >= 0) || max_steps < 1) return fail(MM_EINVAL, "bad rtol, tol or max_steps");
     if (b->pending) return fail(MM_EINVAL, "attempts are already in flight");
     MM_CUDA(cudaSetDevice(b->device));
+    std::fill(b->unstarted.begin(), b->unstarted.end(), 0);
     return b->prec == MM_FP64 ? batch_begin_impl<double>(b, attempts, rtol, tol, max_steps)
                               : batch_begin_impl<float>(b, attempts, rtol, tol, max_steps);
 }

@@ -1,6 +1,8 @@
 """Continuous-batching server for relax requests.
 
-Requests are (arrival time, Workload) pairs with uniform materials.  A request
+Requests are (arrival time, Workload) pairs with uniform materials (and,
+through Workload.extra, an optional uniform DMI "D" of kind "dmi" and the
+"precession" switch, Sec. 4.3 and Sec. 3).  A request
 goes to the size bucket of its grid (shape and cell size); each bucket keeps
 batch states (mm_batch, one CUDA stream each) whose tensor spectrum is built
 once -- the bucket's cached plan -- and whose slots hold one request each.
@@ -136,6 +138,9 @@ class Server:
                                     "torque": float("nan"), "status": self.REJECTED}
                     continue
                 b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0), 1e-13)
+                ex = w.extra or {}
+                if ex.get("D", 0.0) or not ex.get("precession", True):
+                    b.set_slot_terms(slot, ex.get("dmi", "interface"), ex.get("D", 0.0), ex.get("precession", True))
                 occupied[(id(b), slot)] = idx
                 where[idx] = (b, slot)
                 busy.add(id(b))

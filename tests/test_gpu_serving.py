@@ -1,8 +1,9 @@
 """GPU tests of the batched relax path and the continuous-batching server:
 batched FP64 relaxation against the oracle (including a grid with an odd row
-count per grid and a 1-cell grid that is relaxed from the start), FP32
-batched relaxation against the FP64 oracle, and the same result for every
-request alone and in the mix (bitwise: per-grid arithmetic and reductions)."""
+count per grid and a 1-cell grid that is relaxed from the start), slots with
+uniform DMI of each kind and without the precession term, FP32 batched
+relaxation against the FP64 oracle, and the same result for every request
+alone and in the mix (bitwise: per-grid arithmetic and reductions)."""
 import numpy as np
 import pytest
 
@@ -45,6 +46,70 @@ def test_batched_relax_fp64_matches_oracle(n, attempts):
         assert steps[slot] == steps_r
         assert abs(tq[slot] - tq_r) < 1e-6 * tq_r
         assert rel(from_soa(b.get_m(slot)), mr) < 1e-8
+    b.close()
+
+
+TERMS = [("interface", 1.5e-3, True), ("bulk", -1e-3, False), (None, 0.0, False), ("d2d", 2e-3, True)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_relax_with_dmi_and_precession_switch(precision):
+    """Slots with uniform DMI of each kind (Sec. 4.3) and without the precession
+    term (Sec. 3), side by side in one batch, relaxed to max |m x h| / Ms <
+    1e-3 and compared with the oracle's relax of the same problem: FP64 with
+    the same step count, torque and state; FP32 (whose step-size decisions
+    are taken in FP32, so its step sequence may differ) converged to the same
+    state within 1e-2, while the DMI term alone moves the relaxed state by
+    more than 5e-2."""
+    from oracle.llg import Problem, relax
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.workloads import from_soa, to_soa
+    rng = np.random.default_rng(25)
+    n = (12, 8, 2)
+    reqs = [_req(rng, n) for _ in TERMS]
+    b = Batch(n, reqs[0].dx, precision, capacity=len(TERMS))
+    for slot, (w, (kind, D, pc)) in enumerate(zip(reqs, TERMS)):
+        b.set_slot(slot, w.Ms, w.A, w.alpha, to_soa(w.m0))
+        b.set_slot_terms(slot, kind, D, pc)
+    st, steps, tq = _drive(b, 1e-3, 5000, 5)
+    for slot, (w, (kind, D, pc)) in enumerate(zip(reqs, TERMS)):
+        prob = Problem(n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, D=D, dmi=kind or "interface", precession=pc)
+        mr, steps_r, tq_r, _ = relax(prob, w.m0, tol=1e-3, max_steps=5000)
+        assert st[slot] == 2 and tq[slot] < 1e-3
+        mg = from_soa(b.get_m(slot))
+        if precision == "fp64":
+            assert steps[slot] == steps_r, (slot, steps[slot], steps_r)
+            assert abs(tq[slot] - tq_r) < 1e-6 * tq_r
+            assert rel(mg, mr) < 1e-8
+        else:
+            assert rel(mg, mr) < 1e-2
+            if D:
+                prob0 = Problem(n, w.dx, Ms=w.Ms, A=w.A, alpha=w.alpha, precession=pc)
+                m0r, _, _, _ = relax(prob0, w.m0, tol=1e-3, max_steps=5000)
+                assert rel(m0r, mr) > 5e-2
+    b.close()
+
+
+def test_batched_dmi_term_is_applied():
+    """The same request with and without its DMI term ends in different
+    states (the term reaches the field), and a reloaded slot starts without
+    the previous request's terms."""
+    from paper_2302_08843_gb300.binding import Batch
+    from paper_2302_08843_gb300.workloads import to_soa
+    rng = np.random.default_rng(26)
+    n = (10, 6, 1)
+    w = _req(rng, n)
+    b = Batch(n, w.dx, "fp64", capacity=3)
+    b.set_slot(0, w.Ms, w.A, w.alpha, to_soa(w.m0))
+    b.set_slot(1, w.Ms, w.A, w.alpha, to_soa(w.m0))
+    b.set_slot_terms(1, "interface", 3e-3, True)
+    _drive(b, 1e-12, 10, 10)
+    m0, m1 = b.get_m(0), b.get_m(1)
+    assert np.max(np.abs(m0 - m1)) > 1e-6
+    b.clear_slot(1)
+    b.set_slot(1, w.Ms, w.A, w.alpha, to_soa(w.m0))
+    _drive(b, 1e-12, 10, 10)
+    assert np.array_equal(b.get_m(1), m0)
     b.close()
 
 
@@ -92,6 +157,9 @@ def test_same_alone_and_in_the_mix():
     rng = np.random.default_rng(23)
     grids = [(16, 16, 1), (12, 6, 3), (20, 10, 2)]
     reqs = [(0.0, _req(rng, grids[i % 3], "r%d" % i)) for i in range(10)]
+    # some requests carry a DMI term or run without the precession term
+    for i, (kind, D, pc) in zip((1, 4, 5, 8), TERMS):
+        reqs[i][1].extra.update({"dmi": kind, "D": D, "precession": pc})
     mix = Server(precision="fp32", capacity=3, max_states_per_bucket=1, tol=1e-3, max_steps=3000)
     res_mix = mix.run(reqs, realtime=False, keep_m=True)
     mix.close()

@@ -41,6 +41,10 @@ class FakeBatch:
         self.steps[slot] = 0
         self.status[slot] = 1
 
+    def set_slot_terms(self, slot, dmi=None, D=0.0, precession=True):
+        assert self.status[slot] == 1 and self.steps[slot] == 0
+        FakeBatch.terms.append((self.need[slot], dmi, D, precession))
+
     def begin(self, attempts=1, rtol=1e-5, tol=1e-3, max_steps=20000):
         self.attempts = attempts
 
@@ -73,6 +77,7 @@ class FakeBatch:
 def fake(monkeypatch):
     monkeypatch.setattr(binding, "Batch", FakeBatch)
     FakeBatch.live = FakeBatch.peak = FakeBatch.created = FakeBatch.joined_running = 0
+    FakeBatch.terms = []
     return FakeBatch
 
 
@@ -149,3 +154,20 @@ def test_realtime_arrivals_wait_for_their_time(fake):
         assert r["admitted"] >= arr - 1e-9
         assert r["latency"] >= 0
     srv.close()
+
+
+def test_request_terms_reach_their_slot(fake):
+    """A request's DMI and precession switch (Workload.extra) are loaded into
+    its own slot right after the slot's material, before any attempt; requests
+    without them load none."""
+    reqs = _requests(5, 12, [(8, 8, 1), (6, 4, 2)])
+    want = []
+    for i, (_, w) in enumerate(reqs):
+        if i % 3 == 0:
+            w.extra.update({"dmi": "bulk", "D": 1e-3 * (i + 1), "precession": i % 2 == 0})
+            want.append((int(w.Ms // 1e5), "bulk", 1e-3 * (i + 1), i % 2 == 0))
+    srv = Server(precision="fp32", capacity=4, tol=1e-3, max_steps=100)
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    assert all(r["status"] == 2 for r in res)
+    assert sorted(FakeBatch.terms) == sorted(want)
