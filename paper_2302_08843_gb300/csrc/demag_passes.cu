@@ -352,13 +352,7 @@ __device__ __forceinline__ float k5_thick(float a, float b, float ha, float hb) 
 // MAT: per-cell Ms, A and Ku1 maps (any of them may be absent) and
 // non-equidistant layers (Sec. 4.4, per-layer z links); the x-forward input is
 // then Ms_cell * next, and a cell with Ms = 0 carries no field.
-// STG (uniform material only): the cell phase's rows of m (the tile's rows
-// with the y neighbours, the rows of the planes z -/+ 1), m_n and the RK
-// accumulator are fetched by bulk copies into shared memory as soon as the
-// tile's spectrum has arrived, and land while the x-inverse runs.
-__host__ __device__ constexpr int k5_cell_rows(int TY) { return 3 * (TY + 2) + 12 * TY; }
-__host__ __device__ inline size_t k5_cell_off(size_t before_bars) { return (before_bars + 32 + 127) / 128 * 128; }
-template <int LX, int TY, int NSLOT, int PAD, int MINB, bool DMI, bool MAT, bool STG = false>
+template <int LX, int TY, int NSLOT, int PAD, int MINB, bool DMI, bool MAT>
 __global__ void __launch_bounds__((3 * TY / 2) * K5Eng<LX, +1, false>::type::TPL, MINB)
 k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __restrict__ S1, StageParams<float> p,
          int kxb, int nboxes, int slot_bytes) {
@@ -367,7 +361,6 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
     using FF = typename K5Eng<LX, -1, true>::type;
     static_assert(FI::TPL == FF::TPL, "engines must agree on threads per line");
     static_assert(NSLOT == 1 || NSLOT == 2, "one or two TMA slots");
-    static_assert(!STG || (NSLOT == 1 && !DMI && !MAT), "staged cell rows: one slot, uniform material");
     constexpr int NL = 3 * TY / 2;
     constexpr int LS = NL + PAD;
     constexpr int NT = NL * FI::TPL;
@@ -384,15 +377,9 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
     uint64_t* bar = reinterpret_cast<uint64_t*>(smtma + NSLOT * (size_t)slot_bytes + (size_t)k5_work_elems<LX, LS>() * sizeof(C));
     auto wat = [](int e) { return FI::at(e, LS); };   // place of element e of line 0 in the work area
     const uint32_t tx = (uint32_t)(nboxes * kxb * TY * 3 * sizeof(C));
-    // staged rows: [c][TY + 2] of m at z (y0 - 1 .. y0 + TY), then [c][TY] each of m at z - 1,
-    // m at z + 1, m_n and the accumulator
-    float* cellb = STG ? reinterpret_cast<float*>(
-                             smtma + k5_cell_off(NSLOT * (size_t)slot_bytes + (size_t)k5_work_elems<LX, LS>() * sizeof(C)))
-                       : nullptr;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        if (STG) mbar_init(&bar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -427,37 +414,6 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
         }
         const int yt = t % nyt, z = t / nyt;
         const int y0 = yt * TY;
-        const float* accsrc = p.acc_in ? p.acc_in : (p.nk > 0 ? p.kin[0] : nullptr);
-        if constexpr (STG) {
-            // every thread has passed a barrier since the last tile's cell phase read these rows
-            if (tid == 0) {
-                const uint32_t rb = (uint32_t)nx * 4u;
-                uint32_t bytes = 0;
-                for (int pass = 0; pass < 2; ++pass) {
-                    if (pass == 1) {
-                        fence_proxy_async_smem();
-                        mbar_arrive_expect_tx(&bar[2], bytes);
-                    }
-                    auto row = [&](float* dst, const float* src) {
-                        if (pass == 0) bytes += rb; else bulk_load(dst, src, rb, &bar[2]);
-                    };
-                    for (int c = 0; c < 3; ++c) {
-                        for (int r = 0; r < TY + 2; ++r) {
-                            const int y = y0 - 1 + r;
-                            if (y >= 0 && y < ny) row(cellb + (c * (TY + 2) + r) * nx, m + (size_t)c * N + ((size_t)z * ny + y) * nx);
-                        }
-                        for (int yy = 0; yy < TY && y0 + yy < ny; ++yy) {
-                            const size_t o = (size_t)c * N + ((size_t)z * ny + y0 + yy) * nx;
-                            float* base = cellb + (3 * (TY + 2) + c * TY + yy) * nx;
-                            if (z > 0) row(base, m + o - (size_t)nx * ny);
-                            if (z < nz - 1) row(base + 3 * TY * nx, m + o + (size_t)nx * ny);
-                            row(base + 6 * TY * nx, p.mn + o);
-                            if (accsrc) row(base + 9 * TY * nx, accsrc + o);
-                        }
-                    }
-                }
-            }
-        }
         // ---- stage the c2r input: line l = (c, q) pairs rows y0+2q, y0+2q+1 of component c
         for (int idx = tid; idx < NL * KXn; idx += NT) {
             const int l = idx / KXn, k = idx - l * KXn;
@@ -482,17 +438,6 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < FI::NR / 2; ++r) work[wat(j + r * FI::TPL) + line] = v[r];
-        }
-        if constexpr (STG) {
-            const bool okc = mbar_wait_bounded(&bar[2], it & 1);
-            if (__syncthreads_or(!okc)) {
-                if (tid == 0) {
-                    atomicExch(d.err, kErrTmaTimeout);
-                    mbar_wait_bounded(&bar[2], it & 1);                     // the late rows
-                    if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[0], (it + 1) & 1);   // the next spectrum
-                }
-                return;
-            }
         }
         __syncthreads();
         // ---- cell updates: two consecutive x cells per item, float2 loads
@@ -641,26 +586,7 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
                 // FP32 instruction (add/sub/mul/fma .f32x2)
                 const float2* m2 = reinterpret_cast<const float2*>(m);
                 const int i2 = i >> 1, N2 = N >> 1;
-                // m of the two cells at (x0, y + dy, z + dz) (one of dy, dz nonzero at most), from
-                // the staged rows or from global memory; m of one cell at (x0 + dx, y, z)
-                auto mpair = [&](int c, int dy, int dz) -> float2 {
-                    if constexpr (STG) {
-                        const float* r = dz == 0 ? cellb + (c * (TY + 2) + yy + 1 + dy) * nx
-                                                 : cellb + (3 * (TY + 2) + (dz < 0 ? 0 : 3 * TY) + c * TY + yy) * nx;
-                        return *reinterpret_cast<const float2*>(r + x0);
-                    } else {
-                        return m2[c * N2 + i2 + dy * (nx >> 1) + dz * ((nx * ny) >> 1)];
-                    }
-                };
-                auto mone = [&](int c, int dx) -> float {
-                    if constexpr (STG) return cellb[(c * (TY + 2) + yy + 1) * nx + x0 + dx];
-                    else return m[c * N + i + dx];
-                };
-                // row q of the staged m_n (q = 6) or accumulator (q = 9) of component c
-                auto srow = [&](int q, int c) -> float2 {
-                    return *reinterpret_cast<const float2*>(cellb + (3 * (TY + 2) + q * TY + c * TY + yy) * nx + x0);
-                };
-                const float2 mx = mpair(0, 0, 0), my = mpair(1, 0, 0), mz = mpair(2, 0, 0);
+                const float2 mx = m2[i2], my = m2[N2 + i2], mz = m2[2 * N2 + i2];
                 float2 sx, sy, sz;
                 {   // x links: the inner link, then the outer neighbours (a missing
                     // neighbour stands in as the cell itself and adds nothing)
@@ -669,41 +595,33 @@ k5_fused(DemagDims d, const __grid_constant__ CUtensorMap s1_map, float2* __rest
                     sy = f2mul(wx, f2sub(make_float2(my.y, my.x), my));
                     sz = f2mul(wx, f2sub(make_float2(mz.y, mz.x), mz));
                     const bool hl = x0 > 0, hr = x0 + 2 < nx;
-                    const float2 ox = make_float2(hl ? mone(0, -1) : mx.x, hr ? mone(0, 2) : mx.y);
-                    const float2 oy = make_float2(hl ? mone(1, -1) : my.x, hr ? mone(1, 2) : my.y);
-                    const float2 oz = make_float2(hl ? mone(2, -1) : mz.x, hr ? mone(2, 2) : mz.y);
+                    const float2 ox = make_float2(hl ? m[i - 1] : mx.x, hr ? m[i + 2] : mx.y);
+                    const float2 oy = make_float2(hl ? m[N + i - 1] : my.x, hr ? m[N + i + 2] : my.y);
+                    const float2 oz = make_float2(hl ? m[2 * N + i - 1] : mz.x, hr ? m[2 * N + i + 2] : mz.y);
                     sx = f2fma(wx, f2sub(ox, mx), sx);
                     sy = f2fma(wx, f2sub(oy, my), sy);
                     sz = f2fma(wx, f2sub(oz, mz), sz);
                 }
-                auto link = [&](bool cond, int dy, int dz, float id2) {
+                auto link = [&](bool cond, int off2, float id2) {
                     if (cond) {
                         const float2 w = f2s(p.A * id2);
-                        const float2 a = mpair(0, dy, dz), b = mpair(1, dy, dz), c = mpair(2, dy, dz);
+                        const float2 a = m2[i2 + off2], b = m2[N2 + i2 + off2], c = m2[2 * N2 + i2 + off2];
                         sx = f2fma(w, f2sub(a, mx), sx);
                         sy = f2fma(w, f2sub(b, my), sy);
                         sz = f2fma(w, f2sub(c, mz), sz);
                     }
                 };
-                link(y > 0, -1, 0, p.idy2);
-                link(y < ny - 1, 1, 0, p.idy2);
-                link(z > 0, 0, -1, p.idz2);
-                link(z < nz - 1, 0, 1, p.idz2);
-                float2 nX, nY, nZ;
-                if constexpr (STG) {
-                    nX = srow(6, 0); nY = srow(6, 1); nZ = srow(6, 2);
-                } else {
-                    const float2* mn2 = reinterpret_cast<const float2*>(p.mn);
-                    nX = mn2[i2]; nY = mn2[N2 + i2]; nZ = mn2[2 * N2 + i2];
-                }
+                link(y > 0, -(nx >> 1), p.idy2);
+                link(y < ny - 1, nx >> 1, p.idy2);
+                link(z > 0, -((nx * ny) >> 1), p.idz2);
+                link(z < nz - 1, (nx * ny) >> 1, p.idz2);
+                const float2* mn2 = reinterpret_cast<const float2*>(p.mn);
+                const float2 nX = mn2[i2], nY = mn2[N2 + i2], nZ = mn2[2 * N2 + i2];
                 float2 aX = f2s(0.f), aY = f2s(0.f), aZ = f2s(0.f);
+                const float* accsrc = p.acc_in ? p.acc_in : (p.nk > 0 ? p.kin[0] : nullptr);
                 if (accsrc) {
-                    if constexpr (STG) {
-                        aX = srow(9, 0); aY = srow(9, 1); aZ = srow(9, 2);
-                    } else {
-                        const float2* a2 = reinterpret_cast<const float2*>(accsrc);
-                        aX = a2[i2]; aY = a2[N2 + i2]; aZ = a2[2 * N2 + i2];
-                    }
+                    const float2* a2 = reinterpret_cast<const float2*>(accsrc);
+                    aX = a2[i2]; aY = a2[N2 + i2]; aZ = a2[2 * N2 + i2];
                 }
                 const float2 cex = f2s(p.cex_u);
                 float2 hx = f2mul(cex, sx), hy = f2mul(cex, sy), hz = f2mul(cex, sz);
@@ -2199,16 +2117,6 @@ template <typename T, int L> static void launch_x_inv(const DemagDims& d, const 
 // fused K5 launcher (see k5_fused): false if the shape or material does not qualify
 // k5_fused configuration: TMA slots, work-area row padding, resident CTAs per SM
 constexpr int kK5Rows = 2, kK5Slots = 1, kK5Pad = 0, kK5MinBlocks = 8;
-// uniform material on grids with nx <= 256 (nx % 4 == 0): stage the cell
-// phase's rows in shared memory by bulk copies (k5_fused, STG).  Off: the
-// 36 KB of staged rows per tile leave three resident CTAs per SM instead of
-// eight, and the kernel took 194 us instead of 122.5 us on 256x256x64 (186
-// instead of 70 us on 384-point mixed lines); with 24 warps per SM the plain
-// loads' latency is better hidden than the copies save.
-#ifndef MM_K5_STAGE
-#define MM_K5_STAGE 0
-#endif
-constexpr bool kK5Stage = MM_K5_STAGE != 0;
 #ifndef MM_K5_MIXED_MINB
 #define MM_K5_MIXED_MINB 4
 #endif
@@ -2249,16 +2157,10 @@ template <int L> static bool launch_k5(const DemagDims& d, float2* S1, const Sta
         if (!encode_4d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, S1, dims, strides, box)) return false;
         constexpr int NL = 3 * TY / 2;
         const int slot_bytes = (int)(((size_t)nb * w * TY * 3 * sizeof(float2) + 127) / 128 * 128);
-        const size_t before = kK5Slots * (size_t)slot_bytes + (size_t)k5_work_elems<L, NL + kK5Pad>() * sizeof(float2);
-        const float* accsrc = p.acc_in ? p.acc_in : (p.nk > 0 ? p.kin[0] : nullptr);
-        auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-        const bool stg = kK5Stage && kK5Slots == 1 && !mat && !p.dmi && d.nx % 4 == 0 && d.nx <= 256 && al16(p.m) &&
-                         al16(p.mn) && (!accsrc || al16(accsrc));
-        const size_t sm = stg ? k5_cell_off(before) + (size_t)k5_cell_rows(TY) * d.nx * sizeof(float) : before + 16;
+        const size_t sm = kK5Slots * (size_t)slot_bytes + (size_t)k5_work_elems<L, NL + kK5Pad>() * sizeof(float2) + 16;
         if (sm > 220 * 1024) return false;
         auto k = mat ? k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), false, true>
                  : p.dmi ? k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), true, false>
-                 : stg   ? k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), false, false, kK5Stage>
                          : k5_fused<L, TY, kK5Slots, kK5Pad, k5_minb<L>(), false, false>;
         set_smem(k, sm);
         const int threads = NL * K5Eng<L, +1, false>::type::TPL;
