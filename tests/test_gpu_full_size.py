@@ -1,6 +1,8 @@
-"""Parity at the benchmark's full size and launch configuration: one RK4 step
+"""Parity at the benchmark's full sizes and launch configurations: one RK4 step
 of the bulk workload (256x256x64 cells, FP32 fields, the fused TMA path that
-bench.py times) against one RK4 step of the FP64 oracle on the same inputs.
+bench.py times) against one RK4 step of the FP64 oracle on the same inputs;
+the FP32 field and stage derivative on the bulk grid and on the mixed-radix
+192x192x48 grid.
 
 The update m_{n+1} - m_n = dt * sum(b_s k_s) is compared relative to its own
 size: each field evaluation carries <= 1e-5 relative error in FP32, and m is
@@ -107,3 +109,34 @@ def test_thin_film_dp45_fp32_replayed_by_oracle():
     inc = np.max(np.abs(m - w.m0))
     assert np.max(np.abs(mg - m)) < 1e-4 * inc + 1e-6
     s.close()
+
+
+def test_mixed_radix_full_size_stage_derivative_fp32():
+    """The mixed-radix grid the bench times (the bulk construction on
+    192x192x48, padded 384x384x96): the stage derivative read back through
+    mm_llg_rhs runs the fused kernel on the 384-point 6 8 8 x lines (checked
+    from the launch record), the classic 384-point y passes and the two-factor
+    96-point z pass; against the oracle's FP64 llg_rhs of its own field,
+    element by element, and the field of mm_heff likewise: relative max-norm
+    <= 1e-5 for both."""
+    from oracle.llg import llg_rhs
+    from paper_2302_08843_gb300 import workloads as W
+    from paper_2302_08843_gb300.binding import padded_extents, setup_workload
+    from paper_2302_08843_gb300.workloads import from_soa
+    w = W.bulk(n=(192, 192, 48))
+    assert padded_extents(w.n) == (384, 384, 96)
+    s = setup_workload(w, "fp32")
+    m0_gpu = from_soa(to_host(s.get_m()))
+    s.profile_enable(True)
+    k = from_soa(to_host(s.llg_rhs(t=0.0)))
+    prof = s.profile_read()
+    s.profile_enable(False)
+    h = from_soa(to_host(s.heff(t=0.0)))
+    s.close()
+    assert "k5_fused" in prof and "stage_llg" not in prof, prof
+    href = oracle_problem(w).heff(m0_gpu, 0.0)
+    ref = llg_rhs(m0_gpu, href, w.alpha)
+    err_h = float(np.max(np.abs(h - href)) / np.max(np.abs(href)))
+    err_k = float(np.max(np.abs(k - ref)) / np.max(np.abs(ref)))
+    assert err_h < FP32_TOL, err_h
+    assert err_k < FP32_TOL, err_k
